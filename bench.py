@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the pseudo-potential LB step on GB300.
+
+Default workload: D3Q19 BGK, FP32 deviation storage, 256^3 periodic (16.7 M
+cells), psi = 1 - exp(-rho), G = -5, 4th-order force stencil, centred droplet
+R = 40 (tanh profile rho_l = 2.0, rho_g = 0.15, width 2).  A "step" is one
+lattice time step (psi pass + fused stream-collide-force kernel).  Metric:
+MLUPS (million lattice updates per second), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the domain (the
+single-domain path has no data exchange); the JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: lattice, shape (nz, ny, nx), precision, stencil, droplet R
+    "d3q19_256_fp32": dict(lattice=1, shape=(256, 256, 256), precision=1, stencil=4, R=40.0,
+                           desc="D3Q19 BGK FP32-shifted 256^3 periodic, psi=1-exp(-rho), G=-5, "
+                                "4th-order 3-D force stencil, centred droplet R=40"),
+    "d3q19_256_fp32_iso6": dict(lattice=1, shape=(256, 256, 256), precision=1, stencil=6, R=40.0,
+                                desc="D3Q19 BGK FP32-shifted 256^3 periodic, psi=1-exp(-rho), G=-5, "
+                                     "6th-order 3-D force stencil, centred droplet R=40"),
+    "d2q9_64_fp64": dict(lattice=0, shape=(1, 64, 64), precision=0, stencil=4, R=16.0,
+                         desc="D2Q9 BGK FP64 64^2 periodic, psi=1-exp(-rho), G=-5, 4th-order stencil, "
+                              "centred droplet R=16"),
+}
+RHO_L, RHO_G, WIDTH, G, TAU = 2.0, 0.15, 2.0, -5.0, 1.0
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1906_11027_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        e = rec[workload][kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample_run(wl, budget_s, steps):
+    """Time the FP64 oracle for `steps` steps on a box of the workload's lattice,
+    stencil and droplet, its side chosen so the run takes about budget_s.
+
+    Returns (MLUPS, sample description, cores, seconds)."""
+    import oracle
+    nz, ny, nx = wl["shape"]
+    dim = 3 if nz > 1 else 2
+    lat = {0: oracle.D2Q9, 1: oracle.D3Q19}[wl["lattice"]]
+    side = 48 if dim == 3 else 64
+    probe = oracle.Sim(lat, side, side, side if dim == 3 else 1, stencil=wl["stencil"], G=G, tau=TAU)
+    probe.init_droplet(RHO_L, RHO_G, wl["R"] * side / nx, WIDTH)
+    t0 = time.perf_counter()
+    probe.step(2)
+    rate = 2 * probe.N / (time.perf_counter() - t0)  # cell updates per second
+    del probe
+    L = int((budget_s * rate / steps) ** (1.0 / dim))
+    L = max(16, min(nx, (L // 8) * 8))
+    sim = oracle.Sim(lat, L, L, L if dim == 3 else 1, stencil=wl["stencil"], G=G, tau=TAU)
+    sim.init_droplet(RHO_L, RHO_G, wl["R"] * L / nx, WIDTH)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    mlups = sim.N * steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"FP64 oracle on a {L}^{dim} box of the same lattice, stencil and droplet "
+              f"(R scaled by {L}/{nx}), {steps} steps in {dt:.1f} s")
+    return mlups, sample, cores, dt
+
+
+def run_reference(args, world, rank):
+    """The oracle arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    nsteps = args.steps + args.warmup
+    mlups, sample, cores, dt = oracle_sample_run(wl, 120.0, nsteps)
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": round(mlups, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * dt / nsteps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"]},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1906_11027_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    lbm.load()
+    wl = WORKLOADS[args.workload]
+    nz, ny, nx = wl["shape"]
+    cells = nx * ny * nz
+    stream = torch.cuda.Stream()
+    dom = lbm.Domain(nx, ny, nz, lattice=wl["lattice"], stencil=wl["stencil"], G=G, tau=TAU,
+                     precision=wl["precision"], stream=stream, torch_alloc=True)
+    dom.init_droplet(RHO_L, RHO_G, wl["R"], WIDTH)
+    dom.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)  # let the sampler attach before the timed region
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    kernel_ms = dom.step_timed(args.steps)  # CUDA events around every kernel, same stream
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    barrier(world)
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
+    ms_per_step = elapsed_ms / args.steps
+    value = world * cells * args.steps / (elapsed_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel
+    peak, peak_src = measured_peak_gbs()
+    s = 4 if wl["precision"] == 1 else 8
+    Q = lbm.Q_OF[wl["lattice"]]
+    per_cell = {"k_fused": (2 * Q + 1) * s, "k_psi": (Q + 1) * s}
+    dom_k = max(kernel_ms, key=kernel_ms.get)
+    bytes_launch = per_cell[dom_k] * cells
+    achieved = bytes_launch / (kernel_ms[dom_k] * 1e-3) / 1e9
+    traffic = recorded_traffic(dom_k, args.workload)
+    b_alg = dom.bytes_per_update()
+    step_gbs = value / world * 1e6 * b_alg / 1e9
+
+    # end to end through the public API with host buffers: upload the initial
+    # density from pinned host memory, step, read the observables back
+    rho_host = torch.empty(cells, dtype=torch.float64, pin_memory=True).numpy()
+    z, y, x = np.meshgrid(np.arange(nz) - nz // 2, np.arange(ny) - ny // 2, np.arange(nx) - nx // 2,
+                          indexing="ij")
+    r = np.sqrt(x * x + y * y + (z * z if nz > 1 else 0)).ravel()
+    rho_host[:] = 0.5 * (RHO_L + RHO_G) - 0.5 * (RHO_L - RHO_G) * np.tanh(2 * (r - wl["R"]) / WIDTH)
+    del x, y, z, r
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    dom.init_from_rho(rho_host)
+    dom.step(e2e_steps)
+    obs = dom.observables()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e_value = world * cells * e2e_steps / e2e_s / 1e6
+    d2h = (16 + nx) * 8 + 4
+
+    line = {
+        "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if wl["precision"] == 1 else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "cells": cells,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (populations %.2f GB)" % (2 * Q * s * cells / 1e9),
+                   "schedule": "two-pass (psi kernel + fused TMA kernel)"},
+        "roofline": {"bound": "hbm", "kernel": dom_k, "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "algorithmic_bytes_per_cell": per_cell[dom_k], "peak_source": peak_src,
+                     "kernel_ms": {k: round(v, 5) for k, v in kernel_ms.items()}},
+        "step_roofline": {"bytes_per_update": b_alg, "achieved_gbs": round(step_gbs, 1),
+                          "frac": round(step_gbs / peak, 4),
+                          "roofline_mlups": round(peak * 1e9 / b_alg / 1e6, 1)},
+        "clocks": clocks,
+        "gpu_launches": 2 * args.steps,
+        "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": round(8 * cells / e2e_steps, 1),
+                "d2h_bytes_per_step": round(d2h / e2e_steps, 1),
+                "note": f"init_from_rho(host) + step({e2e_steps}) + observables(); mass {obs['mass']:.6e}"},
+    }
+    dom.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, sample, cores, _ = oracle_sample_run(wl, args.cpu_budget, 4)
+        line["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d3q19_256_fp32")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

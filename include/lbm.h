@@ -1,0 +1,195 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) pseudo-potential multiphase lattice
+ * Boltzmann library (liblbm.so).
+ *
+ * The method is the Shan-Chen pseudo-potential LB model as analysed in
+ * Peng, Ayala, Ayala & Wang, "Isotropy and spurious currents in pseudo-potential
+ * multiphase lattice Boltzmann models" (arXiv:1906.11027):
+ *   psi(rho) field potential, interaction force F (Eq. 1) on an isotropic force
+ *   stencil of 4th..10th order (Sec. 2, Eq. 2) or the lattice itself (the paper's
+ *   "consistent implementation", Sec. 3), Guo-forced BGK collision (Eqs. 3-4) or
+ *   its moment-space (MRT) form, and periodic pull streaming (Eq. 3), on the
+ *   D2Q9, D3Q19, D2Q13 and D2Q25 lattices (Table 1).
+ *
+ * Conventions shared by every call:
+ *  - Return value: LBM_OK (0) or a negative LBM_E* code; lbm_strerror() names
+ *    it and lbm_last_error() gives the text of the most recent failure on the
+ *    calling thread.  Outputs are written only on success (except
+ *    LBM_ENOTCONVERGED from the run-to-steady calls, which still fills them).
+ *  - Units: lattice units, dt = dx = 1.  All scalars are double.
+ *  - Host arrays are owned by the caller.  Device memory is owned by the
+ *    library; it is taken from params.dev_alloc / dev_free when given (e.g. the
+ *    PyTorch caching allocator), else from cudaMalloc / cudaFree.
+ *  - Cell layout of every host field: x fastest, then y, then z
+ *    (index = (z * ny + y) * nx + x).  Populations: [Q][cell] (SoA).
+ *  - A context is bound to the device that was current at lbm_create and to
+ *    one CUDA stream; it is not thread-safe.  Step calls are asynchronous and
+ *    stream-ordered; calls that return host data synchronise the stream.
+ *  - Velocity order inside each lattice: the rest vector first, then shells of
+ *    increasing |c|^2; inside a shell, the vectors whose first non-zero
+ *    component is positive in decreasing lexicographic order, each followed by
+ *    its opposite (D2Q9: 0, +x, -x, +y, -y, (1,1), (-1,-1), (1,-1), (-1,1)).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)          /* bad size, tau <= 1/2, unknown enum, NULL pointer */
+#define LBM_EUNSUPPORTED (-2)    /* valid but not provided (e.g. MRT on D2Q13) */
+#define LBM_ENOMEM (-3)          /* the device allocator failed */
+#define LBM_ECUDA (-4)           /* a CUDA runtime/driver call failed */
+#define LBM_ENONFINITE (-5)      /* NaN/Inf in the fields, or a negative P-R sqrt argument */
+#define LBM_ETIMEOUT (-6)        /* a bounded device wait ran out */
+#define LBM_ENOTCONVERGED (-7)   /* run-to-steady reached max_steps */
+#define LBM_EIO (-8)             /* checkpoint file could not be read or written */
+
+/* ---- enums --------------------------------------------------------------- */
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D2Q13 = 2, LBM_D2Q25 = 3 } lbm_lattice;
+
+/* Force stencil by isotropy order (Sec. 2).  LBM_STENCIL_LATTICE uses the
+ * lattice's own velocities and weights as the stencil (Sec. 3): order 4 for
+ * D2Q9 and D3Q19, 6 for D2Q13, 8 for D2Q25.  2-D supports 4, 6, 8, 10; 3-D 4, 6. */
+typedef enum { LBM_STENCIL_LATTICE = 0, LBM_ISO4 = 4, LBM_ISO6 = 6, LBM_ISO8 = 8, LBM_ISO10 = 10 } lbm_stencil;
+
+/* psi(rho): 1 - exp(-rho), or the Peng-Robinson form of Sec. 3,
+ * psi = sqrt(2 (p_EOS - c_s^2 rho) / (G c_s'^2)) with a = 2/49, b = 2/21, R = 1,
+ * omega = 0.344 and T = T_over_Tc * T_c (T_c the critical point of the EOS). */
+typedef enum { LBM_PSI_EXP = 0, LBM_PSI_PENG_ROBINSON = 1 } lbm_psi;
+
+typedef enum { LBM_BGK = 0, LBM_MRT = 1 } lbm_collision;
+
+/* Storage and arithmetic precision of the populations.  LBM_FP32_SHIFTED keeps
+ * f - w_b rho_bar in float (rho_bar = mean density of the initial state);
+ * reductions stay in double. */
+typedef enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 } lbm_precision;
+
+/* Kernel schedule of one time step.  LBM_PATH_AUTO picks the fastest
+ * available; LBM_PATH_TWO_PASS is a psi kernel followed by the fused
+ * stream-collide-force kernel (psi tiles staged by TMA); LBM_PATH_ONE_PASS is a
+ * single kernel that recomputes psi of each tile's halo in shared memory. */
+typedef enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_PASS = 1, LBM_PATH_ONE_PASS = 2 } lbm_path;
+
+/* ---- parameters ------------------------------------------------------------ */
+typedef struct lbm_params {
+    int nx, ny, nz;          /* periodic box; nz = 1 for 2-D lattices; each >= 8 */
+    int lattice;             /* lbm_lattice */
+    int stencil;             /* lbm_stencil */
+    int psi;                 /* lbm_psi */
+    double T_over_Tc;        /* Peng-Robinson only */
+    double G;                /* interaction strength of Eq. 1 (G < 0 attracts; P-R needs G < 0) */
+    double tau;              /* relaxation time, > 1/2 */
+    int collision;           /* lbm_collision */
+    double s_e, s_eps, s_q;  /* MRT rates of the energy, 4th-order and 3rd-order moments, in (0, 2) */
+    int precision;           /* lbm_precision */
+    int path;                /* lbm_path */
+    void* stream;            /* cudaStream_t to run on; NULL: the library creates its own */
+    void* (*dev_alloc)(size_t bytes, void* alloc_ctx);  /* NULL: cudaMalloc */
+    void (*dev_free)(void* ptr, void* alloc_ctx);
+    void* alloc_ctx;
+} lbm_params;
+
+/* Observables of the current state (Sec. 3 measurements):
+ * rho_l = rho at the centre node (nx/2, ny/2, nz/2); rho_g = rho at node 0;
+ * dp = p(rho_l) - p(rho_g) with the bulk pressure p = c_s^2 rho + (G c_s'^2/2) psi^2
+ * (= p_EOS for Peng-Robinson); max_u / mean_u = max and mean over cells of |u|,
+ * u = (sum f c + F/2) / rho; mass = sum rho; mom = sum rho u; thickness =
+ * number of nodes on the x line through the centre with
+ * 1.05 rho_g <= rho <= 0.95 rho_l (the interface-thickness measure of Sec. 3,
+ * meaningful for a flat interface normal to x); step = steps taken. */
+typedef struct lbm_obs {
+    double rho_l, rho_g, dp, max_u, mean_u, mass, mom[3], thickness;
+    int64_t step;
+} lbm_obs;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* ---- single domain ----------------------------------------------------------- */
+
+/* Fills p with the defaults: 64x64 D2Q9, LBM_STENCIL_LATTICE, exp psi, G = -5,
+ * tau = 1, BGK, s_e = 1.64, s_eps = 1.54, s_q = 1.9, FP64, auto path, no stream,
+ * cudaMalloc. */
+int lbm_params_default(lbm_params* p);
+
+/* Validates p, builds the lattice/stencil tables, allocates the two population
+ * buffers, the ghosted psi buffer and the reduction scratch on the current
+ * device, and encodes the TMA descriptor of the psi buffer.  The populations
+ * start at zero; call an lbm_init_* before stepping.  *out is set on success. */
+int lbm_create(const lbm_params* p, lbm_ctx** out);
+
+/* Synchronises the stream and frees everything the context owns. NULL is a no-op. */
+int lbm_destroy(lbm_ctx* ctx);
+
+/* Static droplet (Sec. 3): rho0 = (rl + rg)/2 - (rl - rg)/2 tanh(2 (r - R) / width),
+ * r the periodic distance to the centre node (nx/2, ny/2, nz/2); populations
+ * f = feq(rho0, u = 0) = w_b rho0.  Resets the step counter. */
+int lbm_init_droplet(lbm_ctx* ctx, double rho_l, double rho_g, double R, double width);
+
+/* Flat liquid slab normal to `axis` (0 = x, 1 = y, 2 = z) on [L/4, 3L/4): the same
+ * tanh profile with r = |i - L/2| and R = L/4. */
+int lbm_init_flat(lbm_ctx* ctx, double rho_l, double rho_g, double width, int axis);
+
+/* f = w_b rho0 from a host density field of nx*ny*nz doubles. */
+int lbm_init_from_rho(lbm_ctx* ctx, const double* rho_host);
+
+/* Pre-collision populations f_b(x, n) in double, [Q][cell], to / from host
+ * arrays of Q*nx*ny*nz doubles (the state the step of Eq. 3 acts on). */
+int lbm_get_populations(lbm_ctx* ctx, double* f_host);
+int lbm_set_populations(lbm_ctx* ctx, const double* f_host);
+
+/* Advances n >= 0 time steps (Eq. 3), asynchronously on the context's stream. */
+int lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* Like lbm_step, but without graph replay and with CUDA events recorded on the
+ * context's stream around every kernel; synchronises at the end.  mean_ms
+ * (capacity max_kernels) receives the mean duration of each kernel position of
+ * one step, *nkernels their number; lbm_step_kernel_name() names position i. */
+int lbm_step_timed(lbm_ctx* ctx, int64_t n, double* mean_ms, int max_kernels, int* nkernels);
+const char* lbm_step_kernel_name(const lbm_ctx* ctx, int i);
+
+/* Steps until the change of max|u| between checks taken every `check_every`
+ * steps, divided by check_every, is below tol (FP32 storage adds the floor
+ * 1e-6 max|u| / check_every for its round-off), or until max_steps.  Returns
+ * LBM_ENOTCONVERGED at max_steps.  *steps_out (may be NULL) = steps taken. */
+int lbm_run_to_steady(lbm_ctx* ctx, double tol, int64_t max_steps, int64_t check_every,
+                      int64_t* steps_out);
+
+/* Observables of the current state (see lbm_obs); synchronises.  Returns
+ * LBM_ENONFINITE if any cell holds NaN/Inf or an invalid P-R argument. */
+int lbm_observables(lbm_ctx* ctx, lbm_obs* out);
+
+/* Density (nx*ny*nz) and velocity (3 per cell, xyz, u = (sum f c + F/2)/rho)
+ * to host arrays; either may be NULL.  Synchronises. */
+int lbm_get_fields(lbm_ctx* ctx, double* rho_host, double* u_host);
+
+/* Device pointer and layout of the current population buffer, for callers
+ * that time or inspect the kernels: *elem_bytes = 8 (FP64) or 4 (FP32
+ * deviations), [Q][cell]. */
+int lbm_device_state(lbm_ctx* ctx, const void** f_dev, int* Q, int64_t* ncells, int* elem_bytes);
+
+/* Raw checkpoint: header (magic, version, parameters, step, rho_bar) followed by
+ * the population buffer.  lbm_load needs a context created with the same
+ * parameters and restores a bit-identical trajectory. */
+int lbm_save(lbm_ctx* ctx, const char* path);
+int lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Algorithmic HBM bytes of one lattice update for this context's lattice and
+ * precision: 2 Q s_f + 2 s_psi (one read and one write of every population,
+ * one write and one read of psi). */
+double lbm_bytes_per_update(const lbm_ctx* ctx);
+
+const char* lbm_strerror(int code);
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

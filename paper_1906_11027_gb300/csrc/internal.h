@@ -1,0 +1,93 @@
+// internal.h -- interface between the C-ABI layer (api.cu) and the kernel
+// instantiations (one translation unit per lattice).  Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace lbm {
+
+// Error bits raised by kernels in the device error word.
+enum : unsigned {
+    kErrNonFinite = 1u,   // NaN/Inf density or velocity
+    kErrNegativeSqrt = 2u,  // Peng-Robinson psi argument below zero
+    kErrTimeout = 4u,     // a bounded wait (mbarrier) gave up
+};
+
+// psi buffer: periodic ghost layers, kGhostX cells on each side in x (so that
+// every TMA box starts on a 16-byte boundary) and `g` = stencil radius in y, z.
+constexpr int kGhostX = 4;
+
+// Runtime constants of one domain, passed by value to every kernel.
+struct DevParams {
+    int nx, ny, nz;
+    long long N;         // cells
+    int g;               // ghost width of psi in y (and z)
+    int psx;             // psi row pitch in elements
+    int psy;             // psi rows per z plane (ny + 2g)
+    double G;
+    double omega;        // 1 / tau
+    double pref;         // 1 - 1/(2 tau)
+    double rho_bar;      // reference density of FP32 deviation storage (0 in FP64)
+    int psi_kind;        // 0 exp, 1 Peng-Robinson
+    double pr_T;         // Peng-Robinson temperature T_over_Tc * T_c
+    double pr_alpha;     // alpha(T)
+    double rate[4];      // MRT rates by class: 1/tau, s_e, s_eps, s_q
+    unsigned* err;       // device error word
+};
+
+// Everything a launcher may need; unused fields are ignored.
+struct LaunchArgs {
+    DevParams p;
+    const void* fin;       // populations read (current state)
+    void* fout;            // populations written
+    void* psi;             // ghosted psi buffer (base of the allocation)
+    const CUtensorMap* tmap;  // TMA descriptor of the psi buffer
+    double* partials;      // reduction scratch
+    int nblocks_max;       // capacity of partials (blocks)
+    double* res;           // reduction result (see api.cu for the slots)
+    double* dbuf0;         // double work buffers (N or Q*N)
+    double* dbuf1;
+    int mode;              // init profile: 0 droplet, 1 flat
+    int axis;
+    double a0, a1, a2, a3; // init parameters (rho_l, rho_g, R, width)
+};
+
+// One set of launchers per (lattice, stencil order, collision, precision).
+struct KernelSet {
+    int tile_x, tile_y, tile_z;  // fused-kernel tile (TMA box minus halo)
+    cudaError_t (*psi)(const LaunchArgs&, cudaStream_t);
+    cudaError_t (*fused)(const LaunchArgs&, cudaStream_t);
+    cudaError_t (*onepass)(const LaunchArgs&, cudaStream_t);  // may be null
+    cudaError_t (*obs)(const LaunchArgs&, cudaStream_t, int* nblocks);
+    cudaError_t (*probe)(const LaunchArgs&, cudaStream_t);
+    cudaError_t (*fields)(const LaunchArgs&, cudaStream_t);
+    cudaError_t (*init_profile)(const LaunchArgs&, cudaStream_t);
+    cudaError_t (*init_from_rho)(const LaunchArgs&, cudaStream_t);
+    cudaError_t (*get_f)(const LaunchArgs&, cudaStream_t);
+    cudaError_t (*set_f)(const LaunchArgs&, cudaStream_t);
+    cudaError_t (*rho_of_f)(const LaunchArgs&, cudaStream_t);
+};
+
+// Shared reduction helpers (kernels.cu).
+cudaError_t launch_sum_partials(const double* partials, int nblocks, int width, double* res,
+                                cudaStream_t s);
+cudaError_t launch_mean(const double* x, long long n, double* partials, int nblocks_max,
+                        double* res, cudaStream_t s);
+
+// Per-lattice lookup (defined in kernels_<lattice>.cu). Returns false if the
+// combination is not instantiated.
+bool kernels_d2q9(int order, int coll, int fp32, KernelSet* ks);
+bool kernels_d3q19(int order, int coll, int fp32, KernelSet* ks);
+bool kernels_d2q13(int order, int coll, int fp32, KernelSet* ks);
+bool kernels_d2q25(int order, int coll, int fp32, KernelSet* ks);
+
+// Slots of the reduction result array `res`.
+enum ResSlot {
+    kResMass = 0, kResMomX, kResMomY, kResMomZ, kResSumU, kResMaxU, kResCount,
+    kResRhoCentre = 8, kResRhoOrigin = 9, kResLine = 16  // then nx values
+};
+constexpr int kObsWidth = 6;
+
+}  // namespace lbm

@@ -1,0 +1,722 @@
+// kernels.cuh -- device kernels of one pseudo-potential LB time step and its
+// readbacks, templated on lattice, force-stencil order, collision and precision.
+//
+// Storage: the context keeps the post-collision, not yet streamed populations
+// A_b(y) = f*_b(y, n-1) (pull scheme).  The pre-collision state of Eq. 3 is
+// f_b(x, n) = A_b(x - c_b).  One step (two-pass schedule):
+//   k_psi   : rho(x) = sum_b A_b(x - c_b),  psi(rho) -> ghosted psi buffer
+//   k_fused : TMA-stage the psi tile + halo in shared memory; gather f(x);
+//             rho, j = sum f c; F = -G psi(x) sum_a w_a psi(x + e_a) e_a (Eq. 1);
+//             u = (j + F/2)/rho; Guo-forced BGK or MRT collision (Eqs. 3-4);
+//             write B_b(x) = f*_b(x).
+// FP32 storage keeps deviations f~ = f - w_b rho_bar (rho = rho_bar + sum f~).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace lbm {
+
+constexpr double kPrA = 2.0 / 49.0;  // Peng-Robinson a, b (R = 1), Sec. 3
+constexpr double kPrB = 2.0 / 21.0;
+
+// ---- small PTX helpers: shared-memory mbarrier and TMA ----------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: every try_wait suspends for a hardware-chosen interval, so the
+// bound is a few seconds at most.  Returns false if it ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// ---- indexing -----------------------------------------------------------------
+__device__ __forceinline__ long long cell_of(const DevParams& p, int x, int y, int z)
+{
+    return (static_cast<long long>(z) * p.ny + y) * p.nx + x;
+}
+template <int C>
+__device__ __forceinline__ int shift_wrap(int i, int n)
+{
+    // i - C on a periodic axis, |C| <= 3 <= n
+    int j = i - C;
+    if (C > 0 && j < 0) j += n;
+    if (C < 0 && j >= n) j -= n;
+    return j;
+}
+template <int C>
+__device__ __forceinline__ int shift_wrap_fwd(int i, int n)
+{
+    int j = i + C;
+    if (C < 0 && j < 0) j += n;
+    if (C > 0 && j >= n) j -= n;
+    return j;
+}
+
+// Pull gather of the pre-collision populations f_b(x) = A_b(x - c_b).
+template <int LAT, class Real>
+__device__ __forceinline__ void gather(const Real* __restrict__ A, const DevParams& p, int x, int y, int z,
+                                       Real (&f)[Lattice<LAT>::Q])
+{
+    using L = Lattice<LAT>;
+    sfor<L::Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+        const int xs = shift_wrap<cx>(x, p.nx);
+        const int ys = shift_wrap<cy>(y, p.ny);
+        const int zs = (L::D == 3) ? shift_wrap<cz>(z, p.nz) : 0;
+        f[b] = A[static_cast<long long>(b) * p.N + cell_of(p, xs, ys, zs)];
+    });
+}
+
+// ---- psi -------------------------------------------------------------------------
+__device__ __forceinline__ double psi_exp(double r) { return -expm1(-r); }
+__device__ __forceinline__ float psi_exp(float r) { return -expm1f(-r); }
+
+// psi = sqrt(2 (p_EOS - c_s^2 rho) / (G c_s'^2)) with the Peng-Robinson EOS (Sec. 3).
+__device__ __forceinline__ double psi_pr(double rho, const DevParams& p, double cs2)
+{
+    const double pe = rho * p.pr_T / (1.0 - kPrB * rho)
+                    - kPrA * p.pr_alpha * rho * rho / (1.0 + 2.0 * kPrB * rho - kPrB * kPrB * rho * rho);
+    const double arg = 2.0 * (pe - cs2 * rho) / (p.G * cs2);
+    if (!(arg >= 0.0)) atomicOr(p.err, kErrNegativeSqrt);
+    return sqrt(arg);
+}
+
+template <int LAT, class Real>
+__device__ __forceinline__ Real psi_of(Real rho, const DevParams& p)
+{
+    if (std::is_same<Real, double>::value && p.psi_kind == 1)
+        return static_cast<Real>(psi_pr(static_cast<double>(rho), p, Lattice<LAT>::cs2));
+    return psi_exp(rho);
+}
+
+// Writes psi of cell (x, y, z) and its periodic images into the ghosted buffer.
+template <int D, class Real>
+__device__ __forceinline__ void store_psi(Real* __restrict__ psi, const DevParams& p, int x, int y, int z, Real v)
+{
+    const int g = p.g;
+    const int gz = (D == 3) ? g : 0;
+    const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        const int Z = z + dz * p.nz;
+        if (Z < -gz || Z >= p.nz + gz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int Y = y + dy * p.ny;
+            if (Y < -g || Y >= p.ny + g) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int X = x + dx * p.nx;
+                if (X < -kGhostX || X >= p.nx + kGhostX) continue;
+                psi[(static_cast<long long>(Z + gz) * p.psy + (Y + g)) * p.psx + (X + kGhostX)] = v;
+            }
+        }
+    }
+}
+
+// ---- force (Eq. 1) from a psi view with compile-time strides -------------------
+template <int LAT, int ORD, class Real, int SX, int SY>
+__device__ __forceinline__ void force_from(const Real* tc, double G, Real (&F)[3])
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<L::D, ORD>;
+    Real ax = Real(0), ay = Real(0), az = Real(0);
+    sfor<S::n>([&](auto aI) {
+        constexpr int a = decltype(aI)::value;
+        constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1], ez = S::T.v[a][2];
+        constexpr double wt = S::T.w[a] * L::cs2;  // c_s^2-scaled force weight
+        const Real wp = Real(wt) * tc[(ez * SY + ey) * SX + ex];
+        if (ex != 0) ax += wp * Real(ex);
+        if (ey != 0) ay += wp * Real(ey);
+        if (ez != 0) az += wp * Real(ez);
+    });
+    const Real gp = -Real(G) * tc[0];
+    F[0] = gp * ax;
+    F[1] = gp * ay;
+    F[2] = gp * az;
+}
+
+// ---- collision (Eqs. 3-4) --------------------------------------------------------
+// f holds pre-collision populations (FP32: deviations); on return the
+// post-collision ones.  Returns nothing; rho, u computed inside.
+template <int LAT, int COLL, class Real>
+__device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (&F)[3], const DevParams& p)
+{
+    using L = Lattice<LAT>;
+    constexpr bool kDev = std::is_same<Real, float>::value;  // deviation storage
+    Real s = Real(0), jx = Real(0), jy = Real(0), jz = Real(0);
+    sfor<L::Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+        s += f[b];
+        if (cx != 0) jx += f[b] * Real(cx);
+        if (cy != 0) jy += f[b] * Real(cy);
+        if (cz != 0) jz += f[b] * Real(cz);
+    });
+    const Real rho = kDev ? Real(p.rho_bar) + s : s;
+    const Real ux = (jx + Real(0.5) * F[0]) / rho;
+    const Real uy = (jy + Real(0.5) * F[1]) / rho;
+    const Real uz = (jz + Real(0.5) * F[2]) / rho;
+    constexpr double cs2 = L::cs2;
+    const Real inv_cs2 = Real(1.0 / cs2);
+    const Real inv_cs4 = Real(1.0 / (cs2 * cs2));
+    const Real half_inv_cs4 = Real(0.5 / (cs2 * cs2));
+    const Real usq = (ux * ux + uy * uy + uz * uz) * Real(0.5 / cs2);
+    const Real uF = ux * F[0] + uy * F[1] + uz * F[2];
+    const Real omega = Real(p.omega);
+    const Real pref = Real(p.pref);
+    if constexpr (COLL == 0) {
+        sfor<L::Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+            constexpr double wb = L::T.w[b];
+            const Real w = Real(wb);
+            const Real cu = Real(cx) * ux + Real(cy) * uy + Real(cz) * uz;
+            const Real cF = Real(cx) * F[0] + Real(cy) * F[1] + Real(cz) * F[2];
+            const Real poly = cu * inv_cs2 + cu * cu * half_inv_cs4 - usq;
+            const Real feq = kDev ? w * (s + rho * poly) : rho * w * (Real(1) + poly);
+            const Real src = w * ((cF - uF) * inv_cs2 + cu * cF * inv_cs4);
+            f[b] = f[b] + (feq - f[b]) * omega + pref * src;
+        });
+    } else {
+        // Moment space: f* = f + M^-1 [ -S (m - m_eq) + (I - S/2) M phi~ ],
+        // m_eq := M feq, M^-1 = M^T diag(1/|row|^2) (orthogonal rows).
+        using MB = Mrt<LAT>;
+        Real d[L::Q], src[L::Q];
+        sfor<L::Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+            constexpr double wb = L::T.w[b];
+            const Real w = Real(wb);
+            const Real cu = Real(cx) * ux + Real(cy) * uy + Real(cz) * uz;
+            const Real cF = Real(cx) * F[0] + Real(cy) * F[1] + Real(cz) * F[2];
+            const Real poly = cu * inv_cs2 + cu * cu * half_inv_cs4 - usq;
+            const Real feq = kDev ? w * (s + rho * poly) : rho * w * (Real(1) + poly);
+            d[b] = f[b] - feq;
+            src[b] = w * ((cF - uF) * inv_cs2 + cu * cF * inv_cs4);
+        });
+        Real t[L::Q];
+        sfor<L::Q>([&](auto kI) {
+            constexpr int k = decltype(kI)::value;
+            Real dm = Real(0), ms = Real(0);
+            sfor<L::Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                constexpr double m = MB::B.M[k][b];
+                if (m != 0.0) {
+                    dm += Real(m) * d[b];
+                    ms += Real(m) * src[b];
+                }
+            });
+            constexpr int rc = MB::B.rate_class[k];
+            constexpr double inv_norm = MB::B.inv_norm[k];
+            const Real sk = Real(p.rate[rc]);
+            t[k] = (ms * (Real(1) - Real(0.5) * sk) - sk * dm) * Real(inv_norm);
+        });
+        sfor<L::Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            Real acc = Real(0);
+            sfor<L::Q>([&](auto kI) {
+                constexpr int k = decltype(kI)::value;
+                constexpr double m = MB::B.M[k][b];
+                if (m != 0.0) acc += Real(m) * t[k];
+            });
+            f[b] = f[b] + acc;
+        });
+    }
+}
+
+// ---- kernels -------------------------------------------------------------------------
+
+// rho and psi of every cell (pull gather), written with periodic ghosts.
+template <int LAT, class Real>
+__global__ void __launch_bounds__(256) k_psi(const Real* __restrict__ A, Real* __restrict__ psi, DevParams p)
+{
+    using L = Lattice<LAT>;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    Real f[L::Q];
+    gather<LAT>(A, p, x, y, z, f);
+    Real s = Real(0);
+    sfor<L::Q>([&](auto bI) { s += f[decltype(bI)::value]; });
+    const Real rho = std::is_same<Real, float>::value ? Real(p.rho_bar) + s : s;
+    store_psi<L::D>(psi, p, x, y, z, psi_of<LAT>(rho, p));
+}
+
+// Fused pull-stream / force / collide, psi tile staged by TMA.
+template <int LAT, int ORD, int COLL, class Real, int TY, int TZ>
+__global__ void __launch_bounds__(32 * TY * TZ)
+    k_fused(const __grid_constant__ CUtensorMap tmap, const Real* __restrict__ A, Real* __restrict__ B, DevParams p)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<L::D, ORD>;
+    constexpr int D = L::D;
+    constexpr int R = S::radius;
+    constexpr int SX = 32 + 2 * kGhostX;
+    constexpr int SY = TY + 2 * R;
+    constexpr int SZ = (D == 3) ? TZ + 2 * R : 1;
+    __shared__ alignas(128) Real tile[SZ * SY * SX];
+    __shared__ alignas(8) unsigned long long bar;
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int tid = (tz * TY + ty) * 32 + tx;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY, z0 = (D == 3) ? blockIdx.z * TZ : 0;
+    const uint32_t bar_a = smem_u32(&bar);
+    const uint32_t tile_a = smem_u32(tile);
+    if (tid == 0) {
+        mbar_init(bar_a, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(bar_a, static_cast<uint32_t>(sizeof(tile)));
+        // box origin in buffer coordinates = domain (x0 - kGhostX, y0 - R, z0 - R)
+        if (D == 3)
+            tma_load_3d(tile_a, &tmap, x0, y0, z0, bar_a);
+        else
+            tma_load_2d(tile_a, &tmap, x0, y0, bar_a);
+    }
+    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+    const bool active = x < p.nx && y < p.ny && (D == 2 || z < p.nz);
+    Real f[L::Q];
+    if (active) gather<LAT>(A, p, x, y, z, f);
+    if (!mbar_wait(bar_a, 0)) {
+        if (tid == 0) atomicOr(p.err, kErrTimeout);
+        mbar_wait(bar_a, 0);  // never leave with the copy still landing in shared memory
+        return;
+    }
+    if (!active) return;
+    const Real* tc = tile + ((tz + (D == 3 ? R : 0)) * SY + (ty + R)) * SX + (tx + kGhostX);
+    Real F[3];
+    force_from<LAT, ORD, Real, SX, SY>(tc, p.G, F);
+    collide<LAT, COLL>(f, F, p);
+    const long long c = cell_of(p, x, y, z);
+    sfor<L::Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        B[static_cast<long long>(b) * p.N + c] = f[b];
+    });
+}
+
+// Deterministic block reduction of kObsWidth values (sums, last one a max).
+__device__ __forceinline__ void block_reduce_obs(double (&v)[kObsWidth], double* out)
+{
+    __shared__ double sh[8][kObsWidth];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < kObsWidth - 1; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+        v[kObsWidth - 1] = fmax(v[kObsWidth - 1], __shfl_xor_sync(0xffffffffu, v[kObsWidth - 1], o));
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < kObsWidth; ++i) sh[warp][i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        double acc[kObsWidth];
+#pragma unroll
+        for (int i = 0; i < kObsWidth; ++i) acc[i] = sh[0][i];
+        for (int w = 1; w < nw; ++w) {
+#pragma unroll
+            for (int i = 0; i < kObsWidth - 1; ++i) acc[i] += sh[w][i];
+            acc[kObsWidth - 1] = fmax(acc[kObsWidth - 1], sh[w][kObsWidth - 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < kObsWidth; ++i) out[i] = acc[i];
+    }
+}
+
+// psi at (x + ex, y + ey, z + ez) from the ghosted buffer (|e| <= g).
+template <int D, class Real>
+__device__ __forceinline__ double psi_at(const Real* __restrict__ psi, const DevParams& p, int x, int y, int z)
+{
+    const int gz = (D == 3) ? p.g : 0;
+    return static_cast<double>(psi[(static_cast<long long>(z + gz) * p.psy + (y + p.g)) * p.psx + (x + kGhostX)]);
+}
+
+template <int LAT, int ORD, class Real>
+__device__ __forceinline__ void cell_macro(const Real* __restrict__ A, const Real* __restrict__ psi,
+                                           const DevParams& p, int x, int y, int z, double& rho, double (&mom)[3])
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<L::D, ORD>;
+    Real f[L::Q];
+    gather<LAT>(A, p, x, y, z, f);
+    double s = 0.0, j[3] = {0.0, 0.0, 0.0};
+    sfor<L::Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+        const double fb = static_cast<double>(f[b]);
+        s += fb;
+        j[0] += fb * cx;
+        j[1] += fb * cy;
+        j[2] += fb * cz;
+    });
+    rho = std::is_same<Real, float>::value ? p.rho_bar + s : s;
+    double acc[3] = {0.0, 0.0, 0.0};
+    sfor<S::n>([&](auto aI) {
+        constexpr int a = decltype(aI)::value;
+        constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1], ez = S::T.v[a][2];
+        constexpr double wt = S::T.w[a] * L::cs2;
+        const double wp = wt * psi_at<L::D>(psi, p, x + ex, y + ey, z + ez);
+        acc[0] += wp * ex;
+        acc[1] += wp * ey;
+        acc[2] += wp * ez;
+    });
+    const double gp = -p.G * psi_at<L::D>(psi, p, x, y, z);
+    for (int i = 0; i < 3; ++i) mom[i] = j[i] + 0.5 * (gp * acc[i]);
+}
+
+template <int LAT, int ORD, class Real>
+__global__ void __launch_bounds__(256)
+    k_obs(const Real* __restrict__ A, const Real* __restrict__ psi, DevParams p, double* __restrict__ partials)
+{
+    double v[kObsWidth] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    bool bad = false;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx);
+        const long long r = i / p.nx;
+        const int y = static_cast<int>(r % p.ny);
+        const int z = static_cast<int>(r / p.ny);
+        double rho, mom[3];
+        cell_macro<LAT, ORD>(A, psi, p, x, y, z, rho, mom);
+        const double ux = mom[0] / rho, uy = mom[1] / rho, uz = mom[2] / rho;
+        const double um = sqrt(ux * ux + uy * uy + uz * uz);
+        if (!isfinite(rho) || !isfinite(um)) bad = true;
+        v[0] += rho;
+        v[1] += mom[0];
+        v[2] += mom[1];
+        v[3] += mom[2];
+        v[4] += um;
+        v[5] = fmax(v[5], um);
+    }
+    if (bad) atomicOr(p.err, kErrNonFinite);
+    block_reduce_obs(v, partials + static_cast<long long>(blockIdx.x) * kObsWidth);
+}
+
+// rho at the centre node, node 0 and along the x line through the centre.
+template <int LAT, class Real>
+__global__ void k_probe(const Real* __restrict__ A, DevParams p, double* __restrict__ res)
+{
+    using L = Lattice<LAT>;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > p.nx) return;
+    int x, y, z, slot;
+    if (i < p.nx) {
+        x = i; y = p.ny / 2; z = (L::D == 3) ? p.nz / 2 : 0; slot = kResLine + i;
+    } else {
+        x = 0; y = 0; z = 0; slot = kResRhoOrigin;
+    }
+    Real f[L::Q];
+    gather<LAT>(A, p, x, y, z, f);
+    double s = 0.0;
+    sfor<L::Q>([&](auto bI) { s += static_cast<double>(f[decltype(bI)::value]); });
+    const double rho = std::is_same<Real, float>::value ? p.rho_bar + s : s;
+    res[slot] = rho;
+    if (i == p.nx / 2) res[kResRhoCentre] = rho;
+}
+
+template <int LAT, int ORD, class Real>
+__global__ void __launch_bounds__(256) k_fields(const Real* __restrict__ A, const Real* __restrict__ psi,
+                                                DevParams p, double* __restrict__ rho_out, double* __restrict__ u_out)
+{
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx);
+        const long long r = i / p.nx;
+        const int y = static_cast<int>(r % p.ny);
+        const int z = static_cast<int>(r / p.ny);
+        double rho, mom[3];
+        cell_macro<LAT, ORD>(A, psi, p, x, y, z, rho, mom);
+        if (rho_out) rho_out[i] = rho;
+        if (u_out)
+            for (int k = 0; k < 3; ++k) u_out[3 * i + k] = mom[k] / rho;
+    }
+}
+
+// Minimum-image distance of node index i to the centre node n/2.
+__device__ __forceinline__ double min_image(int i, int n)
+{
+    double d = static_cast<double>(i) - static_cast<double>(n / 2);
+    if (d > 0.5 * n) d -= n;
+    if (d < -0.5 * n) d += n;
+    return d;
+}
+
+// Tanh initial density (Sec. 3): droplet (mode 0) or flat slab (mode 1).
+template <int D>
+__global__ void k_init_profile(DevParams p, int mode, int axis, double rl, double rg, double R, double W,
+                               double* __restrict__ rho0)
+{
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx);
+        const long long r = i / p.nx;
+        const int y = static_cast<int>(r % p.ny);
+        const int z = static_cast<int>(r / p.ny);
+        double dist, rad;
+        if (mode == 0) {
+            const double dx = min_image(x, p.nx), dy = min_image(y, p.ny);
+            const double dz = (D == 3) ? min_image(z, p.nz) : 0.0;
+            dist = sqrt(dx * dx + dy * dy + dz * dz);
+            rad = R;
+        } else {
+            const int L = (axis == 0) ? p.nx : ((axis == 1) ? p.ny : p.nz);
+            const int k = (axis == 0) ? x : ((axis == 1) ? y : z);
+            dist = fabs(min_image(k, L));
+            rad = 0.25 * L;
+        }
+        rho0[i] = 0.5 * (rl + rg) - 0.5 * (rl - rg) * tanh(2.0 * (dist - rad) / W);
+    }
+}
+
+// A_b(y) = w_b rho0(y + c_b)  (FP32: w_b (rho0 - rho_bar)), so that the pulled
+// state is f = feq(rho0, 0).
+template <int LAT, class Real>
+__global__ void __launch_bounds__(256) k_init_from_rho(const double* __restrict__ rho0, DevParams p, Real* __restrict__ A)
+{
+    using L = Lattice<LAT>;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx);
+        const long long r = i / p.nx;
+        const int y = static_cast<int>(r % p.ny);
+        const int z = static_cast<int>(r / p.ny);
+        sfor<L::Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+            const int xs = shift_wrap_fwd<cx>(x, p.nx), ys = shift_wrap_fwd<cy>(y, p.ny);
+            const int zs = (L::D == 3) ? shift_wrap_fwd<cz>(z, p.nz) : 0;
+            constexpr double wb = L::T.w[b];
+            const double rv = rho0[cell_of(p, xs, ys, zs)];
+            const double v = std::is_same<Real, float>::value ? wb * (rv - p.rho_bar) : wb * rv;
+            A[static_cast<long long>(b) * p.N + i] = static_cast<Real>(v);
+        });
+    }
+}
+
+// Pre-collision populations in double, [Q][cell].
+template <int LAT, class Real>
+__global__ void __launch_bounds__(256) k_get_f(const Real* __restrict__ A, DevParams p, double* __restrict__ out)
+{
+    using L = Lattice<LAT>;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx);
+        const long long r = i / p.nx;
+        const int y = static_cast<int>(r % p.ny);
+        const int z = static_cast<int>(r / p.ny);
+        Real f[L::Q];
+        gather<LAT>(A, p, x, y, z, f);
+        sfor<L::Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr double wb = L::T.w[b];
+            const double shift = std::is_same<Real, float>::value ? wb * p.rho_bar : 0.0;
+            out[static_cast<long long>(b) * p.N + i] = static_cast<double>(f[b]) + shift;
+        });
+    }
+}
+
+template <int LAT, class Real>
+__global__ void __launch_bounds__(256) k_set_f(const double* __restrict__ in, DevParams p, Real* __restrict__ A)
+{
+    using L = Lattice<LAT>;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx);
+        const long long r = i / p.nx;
+        const int y = static_cast<int>(r % p.ny);
+        const int z = static_cast<int>(r / p.ny);
+        sfor<L::Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+            const int xs = shift_wrap_fwd<cx>(x, p.nx), ys = shift_wrap_fwd<cy>(y, p.ny);
+            const int zs = (L::D == 3) ? shift_wrap_fwd<cz>(z, p.nz) : 0;
+            constexpr double wb = L::T.w[b];
+            const double shift = std::is_same<Real, float>::value ? wb * p.rho_bar : 0.0;
+            A[static_cast<long long>(b) * p.N + i] =
+                static_cast<Real>(in[static_cast<long long>(b) * p.N + cell_of(p, xs, ys, zs)] - shift);
+        });
+    }
+}
+
+// rho(x) = sum_b f_b(x) of a double population array in the pre-collision layout.
+template <int LAT>
+__global__ void __launch_bounds__(256) k_rho_of_f(const double* __restrict__ in, DevParams p, double* __restrict__ rho)
+{
+    using L = Lattice<LAT>;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        sfor<L::Q>([&](auto bI) { s += in[static_cast<long long>(decltype(bI)::value) * p.N + i]; });
+        rho[i] = s;
+    }
+}
+
+// ---- launchers ---------------------------------------------------------------------------
+inline int grid_1d(long long n, int cap = 152 * 16)
+{
+    long long b = (n + 255) / 256;
+    if (b < 1) b = 1;
+    return static_cast<int>(b < cap ? b : cap);
+}
+
+template <int LAT, class Real>
+cudaError_t launch_psi(const LaunchArgs& a, cudaStream_t s)
+{
+    const dim3 blk(32, 8, 1);
+    const dim3 grd((a.p.nx + 31) / 32, (a.p.ny + 7) / 8, Lattice<LAT>::D == 3 ? a.p.nz : 1);
+    k_psi<LAT, Real><<<grd, blk, 0, s>>>(static_cast<const Real*>(a.fin), static_cast<Real*>(a.psi), a.p);
+    return cudaGetLastError();
+}
+
+template <int LAT, int ORD, int COLL, class Real, int TY, int TZ>
+cudaError_t launch_fused(const LaunchArgs& a, cudaStream_t s)
+{
+    const dim3 blk(32, TY, TZ);
+    const dim3 grd((a.p.nx + 31) / 32, (a.p.ny + TY - 1) / TY, Lattice<LAT>::D == 3 ? (a.p.nz + TZ - 1) / TZ : 1);
+    k_fused<LAT, ORD, COLL, Real, TY, TZ><<<grd, blk, 0, s>>>(*a.tmap, static_cast<const Real*>(a.fin),
+                                                             static_cast<Real*>(a.fout), a.p);
+    return cudaGetLastError();
+}
+
+template <int LAT, int ORD, class Real>
+cudaError_t launch_obs(const LaunchArgs& a, cudaStream_t s, int* nblocks)
+{
+    const int nb = grid_1d(a.p.N, a.nblocks_max);
+    k_obs<LAT, ORD, Real><<<nb, 256, 0, s>>>(static_cast<const Real*>(a.fin), static_cast<const Real*>(a.psi),
+                                             a.p, a.partials);
+    *nblocks = nb;
+    return cudaGetLastError();
+}
+
+template <int LAT, class Real>
+cudaError_t launch_probe(const LaunchArgs& a, cudaStream_t s)
+{
+    const int n = a.p.nx + 1;
+    k_probe<LAT, Real><<<(n + 127) / 128, 128, 0, s>>>(static_cast<const Real*>(a.fin), a.p, a.res);
+    return cudaGetLastError();
+}
+
+template <int LAT, int ORD, class Real>
+cudaError_t launch_fields(const LaunchArgs& a, cudaStream_t s)
+{
+    k_fields<LAT, ORD, Real><<<grid_1d(a.p.N), 256, 0, s>>>(static_cast<const Real*>(a.fin),
+                                                           static_cast<const Real*>(a.psi), a.p, a.dbuf0, a.dbuf1);
+    return cudaGetLastError();
+}
+
+template <int LAT>
+cudaError_t launch_init_profile(const LaunchArgs& a, cudaStream_t s)
+{
+    k_init_profile<Lattice<LAT>::D><<<grid_1d(a.p.N), 256, 0, s>>>(a.p, a.mode, a.axis, a.a0, a.a1, a.a2, a.a3,
+                                                                   a.dbuf0);
+    return cudaGetLastError();
+}
+
+template <int LAT, class Real>
+cudaError_t launch_init_from_rho(const LaunchArgs& a, cudaStream_t s)
+{
+    k_init_from_rho<LAT, Real><<<grid_1d(a.p.N), 256, 0, s>>>(a.dbuf0, a.p, static_cast<Real*>(a.fout));
+    return cudaGetLastError();
+}
+
+template <int LAT, class Real>
+cudaError_t launch_get_f(const LaunchArgs& a, cudaStream_t s)
+{
+    k_get_f<LAT, Real><<<grid_1d(a.p.N), 256, 0, s>>>(static_cast<const Real*>(a.fin), a.p, a.dbuf0);
+    return cudaGetLastError();
+}
+
+template <int LAT, class Real>
+cudaError_t launch_set_f(const LaunchArgs& a, cudaStream_t s)
+{
+    k_set_f<LAT, Real><<<grid_1d(a.p.N), 256, 0, s>>>(a.dbuf0, a.p, static_cast<Real*>(a.fout));
+    return cudaGetLastError();
+}
+
+template <int LAT>
+cudaError_t launch_rho_of_f(const LaunchArgs& a, cudaStream_t s)
+{
+    k_rho_of_f<LAT><<<grid_1d(a.p.N), 256, 0, s>>>(a.dbuf0, a.p, a.dbuf1);
+    return cudaGetLastError();
+}
+
+template <int LAT, int ORD, int COLL, class Real>
+KernelSet make_set()
+{
+    constexpr bool k3 = Lattice<LAT>::D == 3;
+    constexpr int TY = k3 ? 4 : 8;
+    constexpr int TZ = k3 ? 2 : 1;
+    KernelSet k{};
+    k.tile_x = 32;
+    k.tile_y = TY;
+    k.tile_z = TZ;
+    k.psi = &launch_psi<LAT, Real>;
+    k.fused = &launch_fused<LAT, ORD, COLL, Real, TY, TZ>;
+    k.onepass = nullptr;
+    k.obs = &launch_obs<LAT, ORD, Real>;
+    k.probe = &launch_probe<LAT, Real>;
+    k.fields = &launch_fields<LAT, ORD, Real>;
+    k.init_profile = &launch_init_profile<LAT>;
+    k.init_from_rho = &launch_init_from_rho<LAT, Real>;
+    k.get_f = &launch_get_f<LAT, Real>;
+    k.set_f = &launch_set_f<LAT, Real>;
+    k.rho_of_f = &launch_rho_of_f<LAT>;
+    return k;
+}
+
+}  // namespace lbm

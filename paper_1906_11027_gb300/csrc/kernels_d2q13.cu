@@ -1,0 +1,27 @@
+// kernels_d2q13.cu -- kernel instantiations for the D2Q13 lattice.
+#include "kernels.cuh"
+
+namespace lbm {
+
+bool kernels_d2q13(int order, int coll, int fp32, KernelSet* ks)
+{
+    if (order == 4 && coll == 0) {
+        *ks = fp32 ? make_set<kLatD2Q13, 4, 0, float>() : make_set<kLatD2Q13, 4, 0, double>();
+        return true;
+    }
+    if (order == 6 && coll == 0) {
+        *ks = fp32 ? make_set<kLatD2Q13, 6, 0, float>() : make_set<kLatD2Q13, 6, 0, double>();
+        return true;
+    }
+    if (order == 8 && coll == 0) {
+        *ks = fp32 ? make_set<kLatD2Q13, 8, 0, float>() : make_set<kLatD2Q13, 8, 0, double>();
+        return true;
+    }
+    if (order == 10 && coll == 0) {
+        *ks = fp32 ? make_set<kLatD2Q13, 10, 0, float>() : make_set<kLatD2Q13, 10, 0, double>();
+        return true;
+    }
+    return false;
+}
+
+}  // namespace lbm

@@ -1,0 +1,43 @@
+// kernels_d2q9.cu -- kernel instantiations for the D2Q9 lattice.
+#include "kernels.cuh"
+
+namespace lbm {
+
+bool kernels_d2q9(int order, int coll, int fp32, KernelSet* ks)
+{
+    if (order == 4 && coll == 0) {
+        *ks = fp32 ? make_set<kLatD2Q9, 4, 0, float>() : make_set<kLatD2Q9, 4, 0, double>();
+        return true;
+    }
+    if (order == 4 && coll == 1) {
+        *ks = fp32 ? make_set<kLatD2Q9, 4, 1, float>() : make_set<kLatD2Q9, 4, 1, double>();
+        return true;
+    }
+    if (order == 6 && coll == 0) {
+        *ks = fp32 ? make_set<kLatD2Q9, 6, 0, float>() : make_set<kLatD2Q9, 6, 0, double>();
+        return true;
+    }
+    if (order == 6 && coll == 1) {
+        *ks = fp32 ? make_set<kLatD2Q9, 6, 1, float>() : make_set<kLatD2Q9, 6, 1, double>();
+        return true;
+    }
+    if (order == 8 && coll == 0) {
+        *ks = fp32 ? make_set<kLatD2Q9, 8, 0, float>() : make_set<kLatD2Q9, 8, 0, double>();
+        return true;
+    }
+    if (order == 8 && coll == 1) {
+        *ks = fp32 ? make_set<kLatD2Q9, 8, 1, float>() : make_set<kLatD2Q9, 8, 1, double>();
+        return true;
+    }
+    if (order == 10 && coll == 0) {
+        *ks = fp32 ? make_set<kLatD2Q9, 10, 0, float>() : make_set<kLatD2Q9, 10, 0, double>();
+        return true;
+    }
+    if (order == 10 && coll == 1) {
+        *ks = fp32 ? make_set<kLatD2Q9, 10, 1, float>() : make_set<kLatD2Q9, 10, 1, double>();
+        return true;
+    }
+    return false;
+}
+
+}  // namespace lbm
