@@ -185,6 +185,30 @@ int lbm_load(lbm_ctx* ctx, const char* path);
  * one write and one read of psi). */
 double lbm_bytes_per_update(const lbm_ctx* ctx);
 
+/* Mass and momentum totals of a population buffer, computed without allocating
+ * anything.  The paper has no counterpart: this serves callers that cannot
+ * allocate device memory at the moment they need the totals, such as an
+ * application whose device memory is all reserved up front by another
+ * framework's pool, or a service that must not call cudaMalloc on its
+ * latency-critical path.
+ *   f_dev     populations in the library's layout: [Q][cell], the
+ *             post-collision buffer that lbm_device_state returns; double for
+ *             LBM_FP64, float deviations from w_b rho_bar for LBM_FP32_SHIFTED
+ *   lattice, precision, nx, ny, nz, rho_bar   describe that buffer (rho_bar is
+ *             ignored for LBM_FP64)
+ *   stream    cudaStream_t the kernels run on (NULL: the legacy default stream);
+ *             the call synchronises it
+ *   out_host  4 doubles: sum over cells of rho, then of sum_b f_b c_b (x, y, z),
+ *             the momentum before the half-force term
+ * The block partials live in one static device array of about 512 KiB that
+ * every GPU loading the library keeps until exit, so at most 16,777,216 cells
+ * are accepted (LBM_EINVAL beyond, with a message in lbm_last_error()).  The
+ * first call on a device looks the array up with cudaGetSymbolAddress; make it
+ * before any stream capture.  Every call shares the array: calls that overlap
+ * on the GPU race and must be serialised by the caller. */
+int lbm_moments_noalloc(const void* f_dev, int lattice, int precision, int nx, int ny, int nz,
+                        double rho_bar, void* stream, double* out_host);
+
 const char* lbm_strerror(int code);
 const char* lbm_last_error(void);
 

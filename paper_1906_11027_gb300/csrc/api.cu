@@ -110,6 +110,8 @@ constexpr uint32_t kMagic = 0x4c424d31u;  // "LBM1"
 
 }  // namespace
 
+int lbm::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 struct lbm_ctx {
     lbm_params prm;
     LatInfo li;

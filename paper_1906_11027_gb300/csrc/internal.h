@@ -70,7 +70,10 @@ struct KernelSet {
     cudaError_t (*rho_of_f)(const LaunchArgs&, cudaStream_t);
 };
 
-// Shared reduction helpers (kernels.cu).
+// Records msg as the calling thread's lbm_last_error() text and returns code.
+int set_last_error(int code, const char* msg);
+
+// Shared reduction helpers (reduce.cu).
 cudaError_t launch_sum_partials(const double* partials, int nblocks, int width, double* res,
                                 cudaStream_t s);
 cudaError_t launch_mean(const double* x, long long n, double* partials, int nblocks_max,

@@ -92,6 +92,7 @@ _SIGNATURES = {
     "lbm_save": (_I, [_P, ctypes.c_char_p]),
     "lbm_load": (_I, [_P, ctypes.c_char_p]),
     "lbm_bytes_per_update": (_D, [_P]),
+    "lbm_moments_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _dp]),
     "lbm_strerror": (ctypes.c_char_p, [_I]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -227,6 +228,14 @@ def lbm_load(ctx, path: str) -> None:
 
 def lbm_bytes_per_update(ctx) -> float:
     return load().lbm_bytes_per_update(ctx)
+
+
+def lbm_moments_noalloc(f_dev, lattice, precision, nx, ny, nz, rho_bar=0.0, stream=None):
+    """Mass and momentum (4 doubles) of a device population buffer; allocates nothing."""
+    out = np.empty(4)
+    _check(load().lbm_moments_noalloc(f_dev, lattice, precision, nx, ny, nz, rho_bar, stream,
+                                      _dptr(out)), "lbm_moments_noalloc")
+    return out
 
 
 def lbm_strerror(code: int) -> str:
