@@ -71,10 +71,14 @@ typedef enum { LBM_BGK = 0, LBM_MRT = 1 } lbm_collision;
  * reductions stay in double. */
 typedef enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 } lbm_precision;
 
-/* Kernel schedule of one time step.  LBM_PATH_AUTO picks the fastest
- * available; LBM_PATH_TWO_PASS is a psi kernel followed by the fused
- * stream-collide-force kernel (psi tiles staged by TMA); LBM_PATH_ONE_PASS is a
- * single kernel that recomputes psi of each tile's halo in shared memory. */
+/* Kernel schedule of one time step; every schedule gives bit-identical results.
+ * LBM_PATH_TWO_PASS: a psi kernel writes psi (with periodic ghosts) to its own
+ * buffer, then the fused stream-collide-force kernel stages psi tiles plus the
+ * stencil halo into shared memory by TMA.  LBM_PATH_ONE_PASS: one kernel
+ * marches each tile along z (2-D: y), computing psi of the tile and its halo
+ * one slab ahead into a shared-memory ring, so every population is read from
+ * HBM once per step.  LBM_PATH_AUTO: the faster of the two, measured on the
+ * first step (see lbm_schedule_report). */
 typedef enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_PASS = 1, LBM_PATH_ONE_PASS = 2 } lbm_path;
 
 /* ---- parameters ------------------------------------------------------------ */
@@ -153,6 +157,15 @@ int lbm_step(lbm_ctx* ctx, int64_t n);
  * one step, *nkernels their number; lbm_step_kernel_name() names position i. */
 int lbm_step_timed(lbm_ctx* ctx, int64_t n, double* mean_ms, int max_kernels, int* nkernels);
 const char* lbm_step_kernel_name(const lbm_ctx* ctx, int i);
+
+/* Names the step schedule in use and the time per step of every candidate the
+ * autotuner measured, as "chosen=NAME;NAME=ms;..." in buf (NUL-terminated,
+ * truncated to len).  With LBM_PATH_AUTO / LBM_PATH_ONE_PASS the first
+ * lbm_step (or this call) times each compiled variant (tile shape, chunk
+ * length, register cap; and the two-pass schedule under AUTO) on the current
+ * state, without advancing it, and keeps the fastest.  The variants perform the
+ * same arithmetic, so the choice changes speed only. */
+int lbm_schedule_report(lbm_ctx* ctx, char* buf, int len);
 
 /* Steps until the change of max|u| between checks taken every `check_every`
  * steps, divided by check_every, is below tol (FP32 storage adds the floor

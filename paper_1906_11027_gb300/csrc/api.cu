@@ -138,6 +138,11 @@ struct lbm_ctx {
     int64_t step;
     cudaGraphExec_t graph;
     bool graph_valid;
+    int variant;       // step schedule: -1 two-pass (psi + fused TMA kernel), else one-pass variant
+    bool tuned;        // schedule chosen (the autotuner runs on the first step)
+    int n_cand;
+    int cand[kMaxVariants + 1];       // candidate schedules of the autotuner
+    double cand_ms[kMaxVariants + 1]; // their measured milliseconds per step
 
     void* dalloc(size_t bytes)
     {
@@ -190,12 +195,60 @@ int set_device(lbm_ctx* c)
     return LBM_OK;
 }
 
+// Launches schedule v (-1 two-pass, else one-pass variant v) from buffer cur to cur^1.
+int launch_schedule(lbm_ctx* c, int v, const LaunchArgs& a)
+{
+    if (v >= 0) {
+        LBM_CK(c->ks.onepass[v].fn(a, c->stream));
+    } else {
+        LBM_CK(c->ks.psi(a, c->stream));
+        LBM_CK(c->ks.fused(a, c->stream));
+    }
+    return LBM_OK;
+}
+
 int one_step(lbm_ctx* c)
 {
     LaunchArgs a = c->args();
-    LBM_CK(c->ks.psi(a, c->stream));
-    LBM_CK(c->ks.fused(a, c->stream));
+    if (int rc = launch_schedule(c, c->variant, a)) return rc;
     c->cur ^= 1;
+    return LBM_OK;
+}
+
+// Times every candidate schedule on the context's current state (cur -> cur^1,
+// without advancing it: each trial recomputes the same step) with CUDA events on
+// the context's stream, and keeps the fastest.  All candidates perform the same
+// arithmetic, so the choice changes speed only.
+int autotune(lbm_ctx* c)
+{
+    if (c->tuned) return LBM_OK;
+    cudaEvent_t e0, e1;
+    LBM_CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(LBM_ECUDA, "event creation failed");
+    }
+    const LaunchArgs a = c->args();
+    constexpr int kReps = 3;
+    int rc = LBM_OK;
+    int best = -1;
+    for (int i = 0; i < c->n_cand && rc == LBM_OK; ++i) {
+        const int v = c->cand[i];
+        rc = launch_schedule(c, v, a);  // warm-up
+        if (rc == LBM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = fail(LBM_ECUDA, "event record");
+        for (int r = 0; r < kReps && rc == LBM_OK; ++r) rc = launch_schedule(c, v, a);
+        if (rc == LBM_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) rc = fail(LBM_ECUDA, "event record");
+        if (rc == LBM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(LBM_ECUDA, "event sync");
+        float ms = 0.f;
+        if (rc == LBM_OK) cudaEventElapsedTime(&ms, e0, e1);
+        c->cand_ms[i] = ms / kReps;
+        if (rc == LBM_OK && (best < 0 || c->cand_ms[i] < c->cand_ms[best])) best = i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LBM_OK) return rc;
+    c->variant = c->cand[best];
+    c->tuned = true;
     return LBM_OK;
 }
 
@@ -365,7 +418,6 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
         if (!(p->G < 0.0)) return fail(LBM_EINVAL, "Peng-Robinson psi needs G < 0");
         if (!(p->T_over_Tc > 0.0 && p->T_over_Tc < 1.0)) return fail(LBM_EINVAL, "T_over_Tc must lie in (0, 1)");
     }
-    if (p->path == LBM_PATH_ONE_PASS) return fail(LBM_EUNSUPPORTED, "one-pass schedule not built for this case");
     if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr))
         return fail(LBM_EINVAL, "dev_alloc and dev_free must be given together");
 
@@ -379,6 +431,8 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     case LBM_D2Q25: ok = kernels_d2q25(order, p->collision, fp32, &ks); break;
     }
     if (!ok) return fail(LBM_EUNSUPPORTED, "combination not instantiated");
+    if (p->path == LBM_PATH_ONE_PASS && ks.n_onepass == 0)
+        return fail(LBM_EUNSUPPORTED, "one-pass schedule not built for this case");
 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(LBM_ENOMEM, "host allocation failed");
@@ -390,6 +444,12 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     c->ks = ks;
     c->elem = fp32 ? 4 : 8;
     c->N = (long long)p->nx * p->ny * nz;
+    c->n_cand = 0;
+    if (p->path != LBM_PATH_ONE_PASS) c->cand[c->n_cand++] = -1;
+    if (p->path != LBM_PATH_TWO_PASS)
+        for (int v = 0; v < ks.n_onepass; ++v) c->cand[c->n_cand++] = v;
+    c->variant = c->cand[0];
+    c->tuned = c->n_cand == 1;
 
     auto cleanup = [&](int code) {
         lbm_destroy(c);
@@ -592,6 +652,8 @@ int lbm_step(lbm_ctx* c, int64_t n)
 {
     if (!c || n < 0) return fail(LBM_EINVAL, "bad argument");
     if (int rc = set_device(c)) return rc;
+    if (n > 0)
+        if (int rc = autotune(c)) return rc;
     while (n > 0) {
         if (c->graphs_ok && n >= kGraphSteps && c->cur == 0) {
             if (!c->graph_valid)
@@ -612,7 +674,8 @@ int lbm_step_timed(lbm_ctx* c, int64_t n, double* mean_ms, int max_kernels, int*
 {
     if (!c || n < 1 || !mean_ms || max_kernels < 2) return fail(LBM_EINVAL, "bad argument");
     if (int rc = set_device(c)) return rc;
-    constexpr int K = 2;  // psi, fused
+    if (int rc = autotune(c)) return rc;
+    const int K = c->variant >= 0 ? 1 : 2;  // onepass | psi, fused
     std::vector<cudaEvent_t> ev((size_t)n * K + 1);
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(LBM_ECUDA, "event creation failed");
@@ -620,11 +683,18 @@ int lbm_step_timed(lbm_ctx* c, int64_t n, double* mean_ms, int max_kernels, int*
     LBM_CK(cudaEventRecord(ev[0], c->stream));
     for (int64_t i = 0; i < n && rc == LBM_OK; ++i) {
         LaunchArgs a = c->args();
-        if (cudaError_t e = c->ks.psi(a, c->stream)) rc = fail(LBM_ECUDA, "psi: %s", cudaGetErrorString(e));
-        if (rc == LBM_OK) cudaEventRecord(ev[i * K + 1], c->stream);
-        if (rc == LBM_OK)
-            if (cudaError_t e = c->ks.fused(a, c->stream)) rc = fail(LBM_ECUDA, "fused: %s", cudaGetErrorString(e));
-        if (rc == LBM_OK) cudaEventRecord(ev[i * K + 2], c->stream);
+        if (c->variant >= 0) {
+            if (cudaError_t e = c->ks.onepass[c->variant].fn(a, c->stream))
+                rc = fail(LBM_ECUDA, "onepass: %s", cudaGetErrorString(e));
+            if (rc == LBM_OK) cudaEventRecord(ev[i + 1], c->stream);
+        } else {
+            if (cudaError_t e = c->ks.psi(a, c->stream)) rc = fail(LBM_ECUDA, "psi: %s", cudaGetErrorString(e));
+            if (rc == LBM_OK) cudaEventRecord(ev[i * K + 1], c->stream);
+            if (rc == LBM_OK)
+                if (cudaError_t e = c->ks.fused(a, c->stream))
+                    rc = fail(LBM_ECUDA, "fused: %s", cudaGetErrorString(e));
+            if (rc == LBM_OK) cudaEventRecord(ev[i * K + 2], c->stream);
+        }
         c->cur ^= 1;
         c->step += 1;
     }
@@ -647,8 +717,21 @@ int lbm_step_timed(lbm_ctx* c, int64_t n, double* mean_ms, int max_kernels, int*
 
 const char* lbm_step_kernel_name(const lbm_ctx* c, int i)
 {
-    (void)c;
+    if (c && c->variant >= 0) return i == 0 ? "k_onepass" : "";
     return i == 0 ? "k_psi" : (i == 1 ? "k_fused" : "");
+}
+
+int lbm_schedule_report(lbm_ctx* c, char* buf, int len)
+{
+    if (!c || !buf || len < 1) return fail(LBM_EINVAL, "bad argument");
+    if (int rc = set_device(c)) return rc;
+    if (int rc = autotune(c)) return rc;
+    auto name = [c](int v) { return v >= 0 ? c->ks.onepass[v].name : "two_pass"; };
+    int off = std::snprintf(buf, (size_t)len, "chosen=%s", name(c->variant));
+    for (int i = 0; i < c->n_cand && off < len; ++i)
+        off += std::snprintf(buf + off, (size_t)(len - off), ";%s=%.5f", name(c->cand[i]),
+                             c->n_cand > 1 ? c->cand_ms[i] : -1.0);
+    return LBM_OK;
 }
 
 int lbm_observables(lbm_ctx* c, lbm_obs* out)

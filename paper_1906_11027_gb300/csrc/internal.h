@@ -54,12 +54,21 @@ struct LaunchArgs {
     double a0, a1, a2, a3; // init parameters (rho_l, rho_g, R, width)
 };
 
+// One compiled variant of the one-pass step kernel (tile shape, chunk length,
+// minimum resident blocks); the autotuner picks among them.
+struct StepVariant {
+    const char* name;
+    cudaError_t (*fn)(const LaunchArgs&, cudaStream_t);
+};
+constexpr int kMaxVariants = 8;
+
 // One set of launchers per (lattice, stencil order, collision, precision).
 struct KernelSet {
     int tile_x, tile_y, tile_z;  // fused-kernel tile (TMA box minus halo)
     cudaError_t (*psi)(const LaunchArgs&, cudaStream_t);
     cudaError_t (*fused)(const LaunchArgs&, cudaStream_t);
-    cudaError_t (*onepass)(const LaunchArgs&, cudaStream_t);  // may be null
+    int n_onepass;                          // 0: no one-pass schedule
+    StepVariant onepass[kMaxVariants];
     cudaError_t (*obs)(const LaunchArgs&, cudaStream_t, int* nblocks);
     cudaError_t (*probe)(const LaunchArgs&, cudaStream_t);
     cudaError_t (*fields)(const LaunchArgs&, cudaStream_t);

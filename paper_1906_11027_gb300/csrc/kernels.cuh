@@ -170,15 +170,17 @@ __device__ __forceinline__ void force_from(const Real* tc, double G, Real (&F)[3
 {
     using L = Lattice<LAT>;
     using S = Stencil<L::D, ORD>;
+    // Opposite stencil vectors are adjacent: each pair contributes
+    // w e (psi(x + e) - psi(x - e)).
     Real ax = Real(0), ay = Real(0), az = Real(0);
-    sfor<S::n>([&](auto aI) {
-        constexpr int a = decltype(aI)::value;
+    sfor<S::n / 2>([&](auto kI) {
+        constexpr int a = 2 * decltype(kI)::value;
         constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1], ez = S::T.v[a][2];
         constexpr double wt = S::T.w[a] * L::cs2;  // c_s^2-scaled force weight
-        const Real wp = Real(wt) * tc[(ez * SY + ey) * SX + ex];
-        if (ex != 0) ax += wp * Real(ex);
-        if (ey != 0) ay += wp * Real(ey);
-        if (ez != 0) az += wp * Real(ez);
+        const Real d = tc[(ez * SY + ey) * SX + ex] - tc[-((ez * SY + ey) * SX + ex)];
+        if (ex != 0) ax += Real(wt * ex) * d;
+        if (ey != 0) ay += Real(wt * ey) * d;
+        if (ez != 0) az += Real(wt * ez) * d;
     });
     const Real gp = -Real(G) * tc[0];
     F[0] = gp * ax;
@@ -216,17 +218,34 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
     const Real omega = Real(p.omega);
     const Real pref = Real(p.pref);
     if constexpr (COLL == 0) {
-        sfor<L::Q>([&](auto bI) {
-            constexpr int b = decltype(bI)::value;
+        // Velocities come in adjacent opposite pairs (b, b+1), c_{b+1} = -c_b, so
+        // feq and Guo's source split into parts even and odd under c -> -c:
+        //   feq = E + O,  src = Es + Os  for b;   E - O,  Es - Os  for b+1.
+        const Real om1 = Real(1) - omega;
+        {
+            constexpr double w0 = L::T.w[0];
+            const Real feq0 = kDev ? Real(w0) * (s - rho * usq) : rho * Real(w0) * (Real(1) - usq);
+            const Real src0 = -Real(w0) * uF * inv_cs2;
+            f[0] = f[0] * om1 + omega * feq0 + pref * src0;
+        }
+        sfor<(L::Q - 1) / 2>([&](auto kI) {
+            constexpr int b = 1 + 2 * decltype(kI)::value;
             constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+            static_assert(L::T.v[b + 1][0] == -cx && L::T.v[b + 1][1] == -cy && L::T.v[b + 1][2] == -cz,
+                          "opposite velocities must be adjacent");
             constexpr double wb = L::T.w[b];
             const Real w = Real(wb);
             const Real cu = Real(cx) * ux + Real(cy) * uy + Real(cz) * uz;
             const Real cF = Real(cx) * F[0] + Real(cy) * F[1] + Real(cz) * F[2];
-            const Real poly = cu * inv_cs2 + cu * cu * half_inv_cs4 - usq;
-            const Real feq = kDev ? w * (s + rho * poly) : rho * w * (Real(1) + poly);
-            const Real src = w * ((cF - uF) * inv_cs2 + cu * cF * inv_cs4);
-            f[b] = f[b] + (feq - f[b]) * omega + pref * src;
+            const Real wr = w * rho;
+            const Real ev_eq = (kDev ? w * s : wr) + wr * (cu * cu * half_inv_cs4 - usq);
+            const Real od_eq = wr * inv_cs2 * cu;
+            const Real ev_src = w * (cu * cF * inv_cs4 - uF * inv_cs2);
+            const Real od_src = w * inv_cs2 * cF;
+            const Real ev = omega * ev_eq + pref * ev_src;
+            const Real od = omega * od_eq + pref * od_src;
+            f[b] = f[b] * om1 + (ev + od);
+            f[b + 1] = f[b + 1] * om1 + (ev - od);
         });
     } else {
         // Moment space: f* = f + M^-1 [ -S (m - m_eq) + (I - S/2) M phi~ ],
@@ -346,6 +365,201 @@ __global__ void __launch_bounds__(32 * TY * TZ)
         constexpr int b = decltype(bI)::value;
         B[static_cast<long long>(b) * p.N + c] = f[b];
     });
+}
+
+// ---- one-pass schedule ------------------------------------------------------------
+// A CTA owns a tile of the plane normal to the marching axis (3-D: TX x TY cells
+// of an xy plane, marching in z; 2-D: TX cells of an x line, marching in y) and
+// a chunk of ZC slabs along the marching axis.  It keeps psi of the tile plus
+// its stencil halo for the 2R+1 slabs around the current one in a shared-memory
+// ring: before colliding slab m it computes psi of slab m + R (pull gather of
+// the halo-extended tile), so psi never goes to HBM and each population is read
+// from HBM once per step (the second gather for the collision hits L1/L2).
+// Chunks are the slowest grid index, so co-resident CTAs hold neighbouring tiles
+// at the same slabs and their halo reads are shared through L2.
+__host__ __device__ constexpr int ring_slot(int m, int ns) { return (m % ns + ns) % ns; }
+
+__device__ __forceinline__ int wrap_any(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+template <int LAT, int ORD, class Real, int EX, int E, int NS>
+__device__ __forceinline__ void force_ring(const Real* ring, int m, int cx, int cy, double G, Real (&F)[3])
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<L::D, ORD>;
+    constexpr int R = S::radius;
+    const Real* base[2 * R + 1];
+#pragma unroll
+    for (int s = 0; s < 2 * R + 1; ++s) base[s] = ring + ring_slot(m - R + s, NS) * E + cy * EX + cx;
+    Real ax = Real(0), ay = Real(0), az = Real(0);
+    sfor<S::n / 2>([&](auto kI) {
+        constexpr int a = 2 * decltype(kI)::value;
+        constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1], ez = S::T.v[a][2];
+        constexpr int dm = (L::D == 3) ? ez : ey;  // offset along the marching axis
+        constexpr int dq = (L::D == 3) ? ey : 0;   // in-plane offset of the second axis
+        constexpr double wt = S::T.w[a] * L::cs2;
+        const Real d = base[dm + R][dq * EX + ex] - base[R - dm][-(dq * EX + ex)];
+        if (ex != 0) ax += Real(wt * ex) * d;
+        if (ey != 0) ay += Real(wt * ey) * d;
+        if (ez != 0) az += Real(wt * ez) * d;
+    });
+    const Real gp = -Real(G) * base[R][0];
+    F[0] = gp * ax;
+    F[1] = gp * ay;
+    F[2] = gp * az;
+}
+
+// Pull gather through precomputed wrapped offsets: f_b = A_b[zo(cz) + yo(cy) + xo(cx)]
+// where xo[j + RE] = wrap(x - j), yo[j + RE] = wrap(y - j) * nx,
+// zo[j + RE] = wrap(z - j) * nx * ny (RE = lattice reach).
+template <int LAT, class Real, int RE>
+__device__ __forceinline__ void gather_off(const Real* __restrict__ A, long long N, const int (&xo)[2 * RE + 1],
+                                           const int (&yo)[2 * RE + 1], const int (&zo)[2 * RE + 1],
+                                           Real (&f)[Lattice<LAT>::Q])
+{
+    using L = Lattice<LAT>;
+    sfor<L::Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+        f[b] = A[static_cast<long long>(b) * N + (zo[cz + RE] + yo[cy + RE] + xo[cx + RE])];
+    });
+}
+
+template <int RE>
+__device__ __forceinline__ void axis_offsets(int i, int n, int scale, int (&o)[2 * RE + 1])
+{
+#pragma unroll
+    for (int j = -RE; j <= RE; ++j) o[j + RE] = wrap_any(i - j, n) * scale;
+}
+
+template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
+    k_onepass(const Real* __restrict__ A, Real* __restrict__ B, DevParams p, int ntx, int nty)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<L::D, ORD>;
+    constexpr int D = L::D;
+    constexpr int R = S::radius;
+    constexpr int RE = L::reach;
+    constexpr int Q = L::Q;
+    constexpr int NT = TX * TY;
+    constexpr int EX = TX + 2 * R;
+    constexpr int EY = (D == 3) ? TY + 2 * R : 1;
+    constexpr int E = EX * EY;
+    constexpr int H = E - NT;          // halo cells of the extended tile
+    constexpr int NS = 2 * R + 2;      // ring depth: one spare slot, one barrier per slab
+    constexpr bool kStash = (R == 1);  // keep the interior populations for the collision
+    static_assert(H <= NT, "halo larger than the block");
+    __shared__ Real ring[NS * E];
+
+    const int ncol = ntx * nty;
+    const int col = blockIdx.x % ncol;
+    const int chunk = blockIdx.x / ncol;
+    const int x0 = (col % ntx) * TX;
+    const int y0 = (D == 3) ? (col / ntx) * TY : 0;
+    const int nm = (D == 3) ? p.nz : p.ny;
+    const int m0 = chunk * ZC;
+    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const long long plane = static_cast<long long>(p.nx) * p.ny;
+
+    // interior cell of this thread (extended-tile position (tx + R, ty + R))
+    const int ix = x0 + tx, iy = y0 + ty;
+    int ixo[2 * RE + 1], iyo[2 * RE + 1];
+    axis_offsets<RE>(wrap_any(ix, p.nx), p.nx, 1, ixo);
+    if (D == 3) axis_offsets<RE>(wrap_any(iy, p.ny), p.ny, p.nx, iyo);
+    const int i_slot = (D == 3 ? (ty + R) * EX : 0) + tx + R;
+
+    // halo cell of this thread (tid < H): the ring of the extended tile
+    const bool has_halo = tid < H;
+    int hex = 0, hey = 0;
+    if (D == 3) {
+        if (tid < R * EX) {
+            hex = tid % EX; hey = tid / EX;
+        } else if (tid < 2 * R * EX) {
+            hex = (tid - R * EX) % EX; hey = EY - R + (tid - R * EX) / EX;
+        } else {
+            const int h = tid - 2 * R * EX;
+            const int k = h % (2 * R);
+            hey = R + h / (2 * R);
+            hex = (k < R) ? k : TX + k;
+        }
+    } else {
+        hex = (tid < R) ? tid : TX + tid;
+    }
+    int hxo[2 * RE + 1], hyo[2 * RE + 1];
+    axis_offsets<RE>(wrap_any(x0 - R + hex, p.nx), p.nx, 1, hxo);
+    if (D == 3) axis_offsets<RE>(wrap_any(y0 - R + hey, p.ny), p.ny, p.nx, hyo);
+    const int h_slot = hey * EX + hex;
+
+    Real fcur[Q], fnxt[Q];
+
+    // psi of slab m for the extended tile; the interior populations go to fnxt
+    auto psi_slab = [&](int m) {
+        int mo[2 * RE + 1];
+        if (D == 3) {
+            axis_offsets<RE>(wrap_any(m, nm), nm, static_cast<int>(plane), mo);
+        } else {
+            axis_offsets<RE>(wrap_any(m, nm), nm, p.nx, mo);
+        }
+        Real* dst = ring + ring_slot(m, NS) * E;
+        const int zero[2 * RE + 1] = {};
+        {
+            Real s = Real(0);
+            if (D == 3)
+                gather_off<LAT, Real, RE>(A, p.N, ixo, iyo, mo, fnxt);
+            else
+                gather_off<LAT, Real, RE>(A, p.N, ixo, mo, zero, fnxt);
+            sfor<Q>([&](auto bI) { s += fnxt[decltype(bI)::value]; });
+            const Real rho = std::is_same<Real, float>::value ? Real(p.rho_bar) + s : s;
+            dst[i_slot] = psi_of<LAT>(rho, p);
+        }
+        if (has_halo) {
+            Real f[Q];
+            Real s = Real(0);
+            if (D == 3)
+                gather_off<LAT, Real, RE>(A, p.N, hxo, hyo, mo, f);
+            else
+                gather_off<LAT, Real, RE>(A, p.N, hxo, mo, zero, f);
+            sfor<Q>([&](auto bI) { s += f[decltype(bI)::value]; });
+            const Real rho = std::is_same<Real, float>::value ? Real(p.rho_bar) + s : s;
+            dst[h_slot] = psi_of<LAT>(rho, p);
+        }
+    };
+
+    for (int m = m0 - R; m < m0 + R; ++m) {
+        psi_slab(m);
+        if (kStash && m == m0 + R - 1) {
+#pragma unroll
+            for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+        }
+    }
+    const bool active = ix < p.nx && (D == 2 || iy < p.ny);
+    for (int m = m0; m < m1; ++m) {
+        psi_slab(m + R);
+        __syncthreads();
+        if (active) {
+            const int y = (D == 3) ? iy : m;
+            const int z = (D == 3) ? m : 0;
+            if (!kStash) gather<LAT>(A, p, ix, y, z, fcur);
+            Real F[3];
+            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, p.G, F);
+            collide<LAT, COLL>(fcur, F, p);
+            const long long c = cell_of(p, ix, y, z);
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                B[static_cast<long long>(b) * p.N + c] = fcur[b];
+            });
+        }
+        if (kStash) {
+#pragma unroll
+            for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+        }
+    }
 }
 
 // Deterministic block reduction of kObsWidth values (sums, last one a max).
@@ -633,6 +847,19 @@ cudaError_t launch_fused(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB>
+cudaError_t launch_onepass(const LaunchArgs& a, cudaStream_t s)
+{
+    constexpr bool k3 = Lattice<LAT>::D == 3;
+    const int ntx = (a.p.nx + TX - 1) / TX;
+    const int nty = k3 ? (a.p.ny + TY - 1) / TY : 1;
+    const int nm = k3 ? a.p.nz : a.p.ny;
+    const long long nblocks = static_cast<long long>(ntx) * nty * ((nm + ZC - 1) / ZC);
+    k_onepass<LAT, ORD, COLL, Real, TX, TY, ZC, MINB><<<static_cast<unsigned>(nblocks), TX * TY, 0, s>>>(
+        static_cast<const Real*>(a.fin), static_cast<Real*>(a.fout), a.p, ntx, nty);
+    return cudaGetLastError();
+}
+
 template <int LAT, int ORD, class Real>
 cudaError_t launch_obs(const LaunchArgs& a, cudaStream_t s, int* nblocks)
 {
@@ -707,7 +934,28 @@ KernelSet make_set()
     k.tile_z = TZ;
     k.psi = &launch_psi<LAT, Real>;
     k.fused = &launch_fused<LAT, ORD, COLL, Real, TY, TZ>;
-    k.onepass = nullptr;
+    // One-pass variants timed by the autotuner: tile TX x TY (2-D: TX), chunk of
+    // ZC slabs, at least MINB resident blocks per SM (a register cap).
+    k.n_onepass = 0;
+    auto add = [&k](const char* name, cudaError_t (*fn)(const LaunchArgs&, cudaStream_t)) {
+        k.onepass[k.n_onepass].name = name;
+        k.onepass[k.n_onepass].fn = fn;
+        ++k.n_onepass;
+    };
+    if constexpr (k3) {
+        add("onepass_32x8_z16_b2", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 2>);
+        if constexpr (COLL == 0 && std::is_same<Real, float>::value) {
+            add("onepass_32x8_z16_b3", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 3>);
+            add("onepass_32x8_z8_b3", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 8, 3>);
+            add("onepass_32x16_z16_b1", &launch_onepass<LAT, ORD, COLL, Real, 32, 16, 16, 1>);
+            if constexpr (Stencil<3, ORD>::radius == 1)
+                add("onepass_32x4_z16_b4", &launch_onepass<LAT, ORD, COLL, Real, 32, 4, 16, 4>);
+        }
+    } else {
+        add("onepass_128_z16_b1", &launch_onepass<LAT, ORD, COLL, Real, 128, 1, 16, 1>);
+        if constexpr (COLL == 0 && std::is_same<Real, float>::value)
+            add("onepass_256_z16_b2", &launch_onepass<LAT, ORD, COLL, Real, 256, 1, 16, 2>);
+    }
     k.obs = &launch_obs<LAT, ORD, Real>;
     k.probe = &launch_probe<LAT, Real>;
     k.fields = &launch_fields<LAT, ORD, Real>;

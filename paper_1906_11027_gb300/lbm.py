@@ -84,6 +84,7 @@ _SIGNATURES = {
     "lbm_step": (_I, [_P, _L]),
     "lbm_step_timed": (_I, [_P, _L, _dp, _I, ctypes.POINTER(_I)]),
     "lbm_step_kernel_name": (ctypes.c_char_p, [_P, _I]),
+    "lbm_schedule_report": (_I, [_P, ctypes.c_char_p, _I]),
     "lbm_run_to_steady": (_I, [_P, _D, _L, _L, ctypes.POINTER(_L)]),
     "lbm_observables": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_get_fields": (_I, [_P, _dp, _dp]),
@@ -190,6 +191,17 @@ def lbm_step_timed(ctx, n: int):
 
 def lbm_step_kernel_name(ctx, i: int) -> str:
     return load().lbm_step_kernel_name(ctx, i).decode()
+
+
+def lbm_schedule_report(ctx) -> dict:
+    """{'chosen': name, name: ms per step, ...} of the step-schedule autotuner."""
+    buf = ctypes.create_string_buffer(1024)
+    _check(load().lbm_schedule_report(ctx, buf, 1024), "lbm_schedule_report")
+    out = {}
+    for item in buf.value.decode().split(";"):
+        k, v = item.split("=")
+        out[k] = v if k == "chosen" else float(v)
+    return out
 
 
 def lbm_run_to_steady(ctx, tol, max_steps, check_every=1):
@@ -326,6 +338,9 @@ class Domain:
 
     def step(self, n=1):
         lbm_step(self.ctx, n)
+
+    def schedule_report(self):
+        return lbm_schedule_report(self.ctx)
 
     def step_timed(self, n=1):
         return lbm_step_timed(self.ctx, n)

@@ -22,11 +22,11 @@ LAT = {  # binding constant -> oracle constant
 
 
 def pair(lbm, lattice, shape, *, stencil=0, coll=0, G=-5.0, tau=1.0, psi=0, T_over_Tc=0.0,
-         precision=0, s=(1.64, 1.54, 1.9)):
+         precision=0, s=(1.64, 1.54, 1.9), path=0):
     nz, ny, nx = shape
     dom = lbm.Domain(nx, ny, nz, lattice=lattice, stencil=stencil, collision=coll, G=G, tau=tau,
                      psi=psi, T_over_Tc=T_over_Tc, precision=precision,
-                     s_e=s[0], s_eps=s[1], s_q=s[2])
+                     s_e=s[0], s_eps=s[1], s_q=s[2], path=path)
     order = stencil
     ref = oracle.Sim(LAT[lattice], nx, ny, nz, stencil=order, psi=psi, T_over_Tc=T_over_Tc, G=G,
                      tau=tau, coll=coll, s_e=s[0], s_eps=s[1], s_q=s[2])
@@ -37,10 +37,11 @@ def rel_max(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-def test_config_d2q9_64_fp64_1000_steps(lbm):
+@pytest.mark.parametrize("path", [1, 2])
+def test_config_d2q9_64_fp64_1000_steps(lbm, path):
     """D2Q9 BGK tau = 1, FP64, 64x64, psi = 1 - exp(-rho), G = -5, 4th-order stencil,
-    droplet R = 16 (rho_l = 2.0, rho_g = 0.15, width 2): 1000 steps."""
-    dom, ref = pair(lbm, lbm.LBM_D2Q9, (1, 64, 64))
+    droplet R = 16 (rho_l = 2.0, rho_g = 0.15, width 2): 1000 steps, both schedules."""
+    dom, ref = pair(lbm, lbm.LBM_D2Q9, (1, 64, 64), path=path)
     for d in (dom, ref):
         d.init_droplet(2.0, 0.15, 16.0, 2.0)
     dom.step(1000)
@@ -247,3 +248,35 @@ def test_full_size_d3q19_256_fp32_against_oracle(lbm):
     m0 = dom.observables()["mass"]
     dom.step(100)
     assert dom.observables()["mass"] == pytest.approx(m0, rel=1e-6)
+
+
+@pytest.mark.parametrize("lattice,shape,stencil,coll,precision", [
+    (0, (1, 29, 37), 10, 1, 0),
+    (0, (1, 40, 300), 4, 0, 1),
+    (2, (1, 29, 37), 0, 0, 0),
+    (3, (1, 33, 41), 8, 0, 1),
+    (1, (11, 20, 37), 6, 1, 0),
+    (1, (24, 17, 40), 4, 0, 1),
+])
+def test_one_pass_matches_two_pass(lbm, lattice, shape, stencil, coll, precision):
+    """The one-pass schedule (psi recomputed in a shared-memory ring) and the
+    two-pass schedule (psi buffer + TMA tiles) do the same arithmetic."""
+    nz, ny, nx = shape
+    doms = [lbm.Domain(nx, ny, nz, lattice=lattice, stencil=stencil, collision=coll, tau=0.9,
+                       precision=precision, path=path) for path in (1, 2)]
+    for d in doms:
+        d.init_droplet(1.9, 0.15, min(nx, ny) / 4, 2.0)
+        d.step(57)
+    a, b = doms[0].get_f(), doms[1].get_f()
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_one_pass_ragged_3d_against_oracle(lbm):
+    """Chunk and tile edges: 3-D sizes that are not multiples of the 32x8 tile or
+    of the 16-slab chunk, marching across the periodic z boundary."""
+    dom, ref = pair(lbm, lbm.LBM_D3Q19, (35, 13, 45), stencil=6, tau=0.8, path=2)
+    for d in (dom, ref):
+        d.init_droplet(1.9, 0.15, 5.0, 2.0)
+    dom.step(40)
+    ref.step(40)
+    assert rel_max(dom.get_f(), ref.get_f()) <= 1e-12
