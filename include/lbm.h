@@ -167,6 +167,11 @@ const char* lbm_step_kernel_name(const lbm_ctx* ctx, int i);
  * same arithmetic, so the choice changes speed only. */
 int lbm_schedule_report(lbm_ctx* ctx, char* buf, int len);
 
+/* Pins the step schedule to the named candidate (a name lbm_schedule_report
+ * lists, e.g. "two_pass"), skipping the autotuner.  LBM_EINVAL if the name is
+ * not a candidate of this context's path. */
+int lbm_set_schedule(lbm_ctx* ctx, const char* name);
+
 /* Steps until the change of max|u| between checks taken every `check_every`
  * steps, divided by check_every, is below tol (FP32 storage adds the floor
  * 1e-6 max|u| / check_every for its round-off), or until max_steps.  Returns

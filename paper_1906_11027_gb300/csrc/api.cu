@@ -734,6 +734,22 @@ int lbm_schedule_report(lbm_ctx* c, char* buf, int len)
     return LBM_OK;
 }
 
+int lbm_set_schedule(lbm_ctx* c, const char* name)
+{
+    if (!c || !name) return fail(LBM_EINVAL, "NULL argument");
+    for (int i = 0; i < c->n_cand; ++i) {
+        const int v = c->cand[i];
+        const char* nm = v >= 0 ? c->ks.onepass[v].name : "two_pass";
+        if (std::strcmp(nm, name) == 0) {
+            invalidate_graph(c);
+            c->variant = v;
+            c->tuned = true;
+            return LBM_OK;
+        }
+    }
+    return fail(LBM_EINVAL, "schedule %s is not a candidate of this context", name);
+}
+
 int lbm_observables(lbm_ctx* c, lbm_obs* out)
 {
     if (!c || !out) return fail(LBM_EINVAL, "NULL argument");

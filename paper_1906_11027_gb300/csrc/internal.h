@@ -60,7 +60,7 @@ struct StepVariant {
     const char* name;
     cudaError_t (*fn)(const LaunchArgs&, cudaStream_t);
 };
-constexpr int kMaxVariants = 8;
+constexpr int kMaxVariants = 12;
 
 // One set of launchers per (lattice, stencil order, collision, precision).
 struct KernelSet {

@@ -81,6 +81,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// Asynchronous 4-byte global -> shared copies (cp.async, completion by groups).
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // ---- indexing -----------------------------------------------------------------
 __device__ __forceinline__ long long cell_of(const DevParams& p, int x, int y, int z)
 {
@@ -196,19 +205,22 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
 {
     using L = Lattice<LAT>;
     constexpr bool kDev = std::is_same<Real, float>::value;  // deviation storage
-    Real s = Real(0), jx = Real(0), jy = Real(0), jz = Real(0);
-    sfor<L::Q>([&](auto bI) {
-        constexpr int b = decltype(bI)::value;
+    // Moments through the opposite pairs (b, b+1): sum f and sum (f_b - f_b+1) c_b.
+    Real s = f[0], jx = Real(0), jy = Real(0), jz = Real(0);
+    sfor<(L::Q - 1) / 2>([&](auto kI) {
+        constexpr int b = 1 + 2 * decltype(kI)::value;
         constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
-        s += f[b];
-        if (cx != 0) jx += f[b] * Real(cx);
-        if (cy != 0) jy += f[b] * Real(cy);
-        if (cz != 0) jz += f[b] * Real(cz);
+        s += f[b] + f[b + 1];
+        const Real d = f[b] - f[b + 1];
+        if (cx != 0) jx += Real(cx) * d;
+        if (cy != 0) jy += Real(cy) * d;
+        if (cz != 0) jz += Real(cz) * d;
     });
     const Real rho = kDev ? Real(p.rho_bar) + s : s;
-    const Real ux = (jx + Real(0.5) * F[0]) / rho;
-    const Real uy = (jy + Real(0.5) * F[1]) / rho;
-    const Real uz = (jz + Real(0.5) * F[2]) / rho;
+    const Real inv_rho = Real(1) / rho;
+    const Real ux = (jx + Real(0.5) * F[0]) * inv_rho;
+    const Real uy = (jy + Real(0.5) * F[1]) * inv_rho;
+    const Real uz = (jz + Real(0.5) * F[2]) * inv_rho;
     constexpr double cs2 = L::cs2;
     const Real inv_cs2 = Real(1.0 / cs2);
     const Real inv_cs4 = Real(1.0 / (cs2 * cs2));
@@ -218,15 +230,25 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
     const Real omega = Real(p.omega);
     const Real pref = Real(p.pref);
     if constexpr (COLL == 0) {
-        // Velocities come in adjacent opposite pairs (b, b+1), c_{b+1} = -c_b, so
-        // feq and Guo's source split into parts even and odd under c -> -c:
-        //   feq = E + O,  src = Es + Os  for b;   E - O,  Es - Os  for b+1.
+        // omega feq_b + pref src_b regrouped (Eq. 4):
+        //   w_b [ A0 + (c.u)(c.V) + c.P ],
+        //   A0 = omega rho (1 - u.u/(2 cs2)) - pref u.F / cs2   (FP32: omega (rho - rho_bar) in
+        //        place of omega rho for the constant term),
+        //   P  = (omega rho u + pref F) / cs2,   V = (omega rho u / 2 + pref F) / cs4;
+        // the c.P term is odd under c -> -c, the rest even.
+        const Real orho = omega * rho;
+        const Real A0 = (kDev ? omega * s : orho) - orho * usq - pref * uF * inv_cs2;
+        const Real Px = (orho * ux + pref * F[0]) * inv_cs2;
+        const Real Py = (orho * uy + pref * F[1]) * inv_cs2;
+        const Real Pz = (orho * uz + pref * F[2]) * inv_cs2;
+        const Real h = Real(0.5) * orho;
+        const Real Vx = (h * ux + pref * F[0]) * inv_cs4;
+        const Real Vy = (h * uy + pref * F[1]) * inv_cs4;
+        const Real Vz = (h * uz + pref * F[2]) * inv_cs4;
         const Real om1 = Real(1) - omega;
         {
             constexpr double w0 = L::T.w[0];
-            const Real feq0 = kDev ? Real(w0) * (s - rho * usq) : rho * Real(w0) * (Real(1) - usq);
-            const Real src0 = -Real(w0) * uF * inv_cs2;
-            f[0] = f[0] * om1 + omega * feq0 + pref * src0;
+            f[0] = f[0] * om1 + Real(w0) * A0;
         }
         sfor<(L::Q - 1) / 2>([&](auto kI) {
             constexpr int b = 1 + 2 * decltype(kI)::value;
@@ -234,18 +256,12 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
             static_assert(L::T.v[b + 1][0] == -cx && L::T.v[b + 1][1] == -cy && L::T.v[b + 1][2] == -cz,
                           "opposite velocities must be adjacent");
             constexpr double wb = L::T.w[b];
-            const Real w = Real(wb);
             const Real cu = Real(cx) * ux + Real(cy) * uy + Real(cz) * uz;
-            const Real cF = Real(cx) * F[0] + Real(cy) * F[1] + Real(cz) * F[2];
-            const Real wr = w * rho;
-            const Real ev_eq = (kDev ? w * s : wr) + wr * (cu * cu * half_inv_cs4 - usq);
-            const Real od_eq = wr * inv_cs2 * cu;
-            const Real ev_src = w * (cu * cF * inv_cs4 - uF * inv_cs2);
-            const Real od_src = w * inv_cs2 * cF;
-            const Real ev = omega * ev_eq + pref * ev_src;
-            const Real od = omega * od_eq + pref * od_src;
-            f[b] = f[b] * om1 + (ev + od);
-            f[b + 1] = f[b + 1] * om1 + (ev - od);
+            const Real cV = Real(cx) * Vx + Real(cy) * Vy + Real(cz) * Vz;
+            const Real cP = Real(cx) * Px + Real(cy) * Py + Real(cz) * Pz;
+            const Real ev = cu * cV + A0;
+            f[b] = f[b] * om1 + Real(wb) * (ev + cP);
+            f[b + 1] = f[b + 1] * om1 + Real(wb) * (ev - cP);
         });
     } else {
         // Moment space: f* = f + M^-1 [ -S (m - m_eq) + (I - S/2) M phi~ ],
@@ -377,7 +393,11 @@ __global__ void __launch_bounds__(32 * TY * TZ)
 // from HBM once per step (the second gather for the collision hits L1/L2).
 // Chunks are the slowest grid index, so co-resident CTAs hold neighbouring tiles
 // at the same slabs and their halo reads are shared through L2.
-__host__ __device__ constexpr int ring_slot(int m, int ns) { return (m % ns + ns) % ns; }
+// Ring slot of slab m (m >= -3): a modulo by a compile-time constant.
+__host__ __device__ constexpr int ring_slot(int m, int ns)
+{
+    return static_cast<int>(static_cast<unsigned>(m + 4 * ns) % static_cast<unsigned>(ns));
+}
 
 __device__ __forceinline__ int wrap_any(int i, int n)
 {
@@ -412,11 +432,45 @@ __device__ __forceinline__ void force_ring(const Real* ring, int m, int cx, int 
     F[2] = gp * az;
 }
 
+// Per-direction base pointers of the population buffers, passed by value so
+// they sit in the kernel's parameter (constant) bank: the address of f_b at
+// cell offset o is one multiply-add on in[b].
+template <class Real, int Q>
+struct Pops {
+    const Real* in[Q];
+    Real* out[Q];
+};
+
+template <class Real, int Q>
+Pops<Real, Q> make_pops(const void* fin, void* fout, long long N)
+{
+    Pops<Real, Q> P;
+    for (int b = 0; b < Q; ++b) {
+        P.in[b] = static_cast<const Real*>(fin) + static_cast<long long>(b) * N;
+        P.out[b] = static_cast<Real*>(fout) + static_cast<long long>(b) * N;
+    }
+    return P;
+}
+
+// i - j on a periodic axis of length n for |j| <= 3 <= n, without a division.
+__device__ __forceinline__ int wrap_near(int i, int n)
+{
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// o[j + RE] = wrap(i - j) * scale for j = -RE..RE, with i already in [0, n).
+template <int RE>
+__device__ __forceinline__ void axis_offsets(int i, int n, int scale, int (&o)[2 * RE + 1])
+{
+#pragma unroll
+    for (int j = -RE; j <= RE; ++j) o[j + RE] = wrap_near(i - j, n) * scale;
+}
+
 // Pull gather through precomputed wrapped offsets: f_b = A_b[zo(cz) + yo(cy) + xo(cx)]
-// where xo[j + RE] = wrap(x - j), yo[j + RE] = wrap(y - j) * nx,
-// zo[j + RE] = wrap(z - j) * nx * ny (RE = lattice reach).
+// where xo[j + RE] = wrap(x - j), yo[j + RE] = wrap(y - j) * nx, and zo likewise
+// (RE = lattice reach).  All offsets are within one direction's array (< 2^31).
 template <int LAT, class Real, int RE>
-__device__ __forceinline__ void gather_off(const Real* __restrict__ A, long long N, const int (&xo)[2 * RE + 1],
+__device__ __forceinline__ void gather_off(const Pops<Real, Lattice<LAT>::Q>& P, const int (&xo)[2 * RE + 1],
                                            const int (&yo)[2 * RE + 1], const int (&zo)[2 * RE + 1],
                                            Real (&f)[Lattice<LAT>::Q])
 {
@@ -424,20 +478,16 @@ __device__ __forceinline__ void gather_off(const Real* __restrict__ A, long long
     sfor<L::Q>([&](auto bI) {
         constexpr int b = decltype(bI)::value;
         constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
-        f[b] = A[static_cast<long long>(b) * N + (zo[cz + RE] + yo[cy + RE] + xo[cx + RE])];
+        f[b] = __ldg(P.in[b] + (zo[cz + RE] + yo[cy + RE] + xo[cx + RE]));
     });
 }
 
-template <int RE>
-__device__ __forceinline__ void axis_offsets(int i, int n, int scale, int (&o)[2 * RE + 1])
-{
-#pragma unroll
-    for (int j = -RE; j <= RE; ++j) o[j + RE] = wrap_any(i - j, n) * scale;
-}
-
-template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB>
+// ST selects where the interior populations wait between their gather for psi
+// (slab m + R) and their collision (R slabs later): 0 = gathered again (L1/L2),
+// 1 = registers (R = 1 only), 2 = dynamic shared memory, [R + 1][Q][TX*TY].
+template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB, int ST>
 __global__ void __launch_bounds__(TX * TY, MINB)
-    k_onepass(const Real* __restrict__ A, Real* __restrict__ B, DevParams p, int ntx, int nty)
+    k_onepass(const __grid_constant__ Pops<Real, Lattice<LAT>::Q> P, DevParams p, int ntx, int nty)
 {
     using L = Lattice<LAT>;
     using S = Stencil<L::D, ORD>;
@@ -451,9 +501,14 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     constexpr int E = EX * EY;
     constexpr int H = E - NT;          // halo cells of the extended tile
     constexpr int NS = 2 * R + 2;      // ring depth: one spare slot, one barrier per slab
-    constexpr bool kStash = (R == 1);  // keep the interior populations for the collision
+    constexpr bool kStash = (ST == 1);
+    constexpr bool kSmem = (ST == 2);
+    constexpr int NST = R + 1;         // shared-memory stash slots
     static_assert(H <= NT, "halo larger than the block");
+    static_assert(ST != 1 || R == 1, "register stash needs a radius-1 stencil");
     __shared__ Real ring[NS * E];
+    extern __shared__ unsigned char dyn_smem[];
+    Real* stash = reinterpret_cast<Real*>(dyn_smem);  // [NST][Q][NT] when kSmem
 
     const int ncol = ntx * nty;
     const int col = blockIdx.x % ncol;
@@ -463,9 +518,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     const int nm = (D == 3) ? p.nz : p.ny;
     const int m0 = chunk * ZC;
     const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const int mscale = (D == 3) ? p.nx * p.ny : p.nx;  // offset of one slab
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const long long plane = static_cast<long long>(p.nx) * p.ny;
 
     // interior cell of this thread (extended-tile position (tx + R, ty + R))
     const int ix = x0 + tx, iy = y0 + ty;
@@ -495,36 +550,39 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     axis_offsets<RE>(wrap_any(x0 - R + hex, p.nx), p.nx, 1, hxo);
     if (D == 3) axis_offsets<RE>(wrap_any(y0 - R + hey, p.ny), p.ny, p.nx, hyo);
     const int h_slot = hey * EX + hex;
+    const int zero[2 * RE + 1] = {};
 
     Real fcur[Q], fnxt[Q];
 
     // psi of slab m for the extended tile; the interior populations go to fnxt
     auto psi_slab = [&](int m) {
         int mo[2 * RE + 1];
-        if (D == 3) {
-            axis_offsets<RE>(wrap_any(m, nm), nm, static_cast<int>(plane), mo);
-        } else {
-            axis_offsets<RE>(wrap_any(m, nm), nm, p.nx, mo);
-        }
+        axis_offsets<RE>(wrap_near(m, nm), nm, mscale, mo);
         Real* dst = ring + ring_slot(m, NS) * E;
-        const int zero[2 * RE + 1] = {};
         {
-            Real s = Real(0);
             if (D == 3)
-                gather_off<LAT, Real, RE>(A, p.N, ixo, iyo, mo, fnxt);
+                gather_off<LAT, Real, RE>(P, ixo, iyo, mo, fnxt);
             else
-                gather_off<LAT, Real, RE>(A, p.N, ixo, mo, zero, fnxt);
+                gather_off<LAT, Real, RE>(P, ixo, mo, zero, fnxt);
+            Real s = Real(0);
             sfor<Q>([&](auto bI) { s += fnxt[decltype(bI)::value]; });
             const Real rho = std::is_same<Real, float>::value ? Real(p.rho_bar) + s : s;
             dst[i_slot] = psi_of<LAT>(rho, p);
+            if (kSmem) {
+                Real* st = stash + static_cast<unsigned>(m + 4 * NST) % NST * (Q * NT) + tid;
+                sfor<Q>([&](auto bI) {
+                    constexpr int bb = decltype(bI)::value;
+                    st[bb * NT] = fnxt[bb];
+                });
+            }
         }
         if (has_halo) {
             Real f[Q];
-            Real s = Real(0);
             if (D == 3)
-                gather_off<LAT, Real, RE>(A, p.N, hxo, hyo, mo, f);
+                gather_off<LAT, Real, RE>(P, hxo, hyo, mo, f);
             else
-                gather_off<LAT, Real, RE>(A, p.N, hxo, mo, zero, f);
+                gather_off<LAT, Real, RE>(P, hxo, mo, zero, f);
+            Real s = Real(0);
             sfor<Q>([&](auto bI) { s += f[decltype(bI)::value]; });
             const Real rho = std::is_same<Real, float>::value ? Real(p.rho_bar) + s : s;
             dst[h_slot] = psi_of<LAT>(rho, p);
@@ -539,20 +597,32 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         }
     }
     const bool active = ix < p.nx && (D == 2 || iy < p.ny);
+    const int cell_xy = (D == 3) ? iy * p.nx + ix : ix;
     for (int m = m0; m < m1; ++m) {
         psi_slab(m + R);
         __syncthreads();
         if (active) {
-            const int y = (D == 3) ? iy : m;
-            const int z = (D == 3) ? m : 0;
-            if (!kStash) gather<LAT>(A, p, ix, y, z, fcur);
+            if (kSmem) {
+                const Real* st = stash + static_cast<unsigned>(m + 4 * NST) % NST * (Q * NT) + tid;
+                sfor<Q>([&](auto bI) {
+                    constexpr int bb = decltype(bI)::value;
+                    fcur[bb] = st[bb * NT];
+                });
+            } else if (!kStash) {
+                int mo[2 * RE + 1];
+                axis_offsets<RE>(m, nm, mscale, mo);
+                if (D == 3)
+                    gather_off<LAT, Real, RE>(P, ixo, iyo, mo, fcur);
+                else
+                    gather_off<LAT, Real, RE>(P, ixo, mo, zero, fcur);
+            }
             Real F[3];
             force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, p.G, F);
             collide<LAT, COLL>(fcur, F, p);
-            const long long c = cell_of(p, ix, y, z);
+            const int c = m * mscale + cell_xy;
             sfor<Q>([&](auto bI) {
                 constexpr int b = decltype(bI)::value;
-                B[static_cast<long long>(b) * p.N + c] = fcur[b];
+                P.out[b][c] = fcur[b];
             });
         }
         if (kStash) {
@@ -560,6 +630,154 @@ __global__ void __launch_bounds__(TX * TY, MINB)
             for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
         }
     }
+}
+
+// One-pass schedule with asynchronous staging (FP32 hot path): the populations
+// of slab s (interior and halo cells of the tile) are copied global -> shared
+// with cp.async one iteration before psi of slab s is formed, and the interior
+// ones stay staged until slab s collides R iterations later.  Load latency is
+// then off the critical path without holding registers.
+// Shared memory: interior [R+2][Q][NT], halo [2][Q][H] (dynamic), psi ring (static).
+template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
+    k_onepass_async(const __grid_constant__ Pops<Real, Lattice<LAT>::Q> P, DevParams p, int ntx, int nty)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<L::D, ORD>;
+    constexpr int D = L::D;
+    constexpr int R = S::radius;
+    constexpr int RE = L::reach;
+    constexpr int Q = L::Q;
+    constexpr int NT = TX * TY;
+    constexpr int EX = TX + 2 * R;
+    constexpr int EY = (D == 3) ? TY + 2 * R : 1;
+    constexpr int E = EX * EY;
+    constexpr int H = E - NT;
+    constexpr int NS = 2 * R + 2;
+    constexpr int NI = R + 2;  // interior staging slots
+    static_assert(H <= NT, "halo larger than the block");
+    static_assert(sizeof(Real) == 4, "4-byte cp.async staging");
+    __shared__ Real ring[NS * E];
+    extern __shared__ unsigned char dyn_smem[];
+    Real* stI = reinterpret_cast<Real*>(dyn_smem);  // [NI][Q][NT]
+    Real* stH = stI + NI * Q * NT;                  // [2][Q][H]
+
+    const int ncol = ntx * nty;
+    const int col = blockIdx.x % ncol;
+    const int chunk = blockIdx.x / ncol;
+    const int x0 = (col % ntx) * TX;
+    const int y0 = (D == 3) ? (col / ntx) * TY : 0;
+    const int nm = (D == 3) ? p.nz : p.ny;
+    const int m0 = chunk * ZC;
+    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const int mscale = (D == 3) ? p.nx * p.ny : p.nx;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+
+    const int ix = x0 + tx, iy = y0 + ty;
+    int ixo[2 * RE + 1], iyo[2 * RE + 1];
+    axis_offsets<RE>(wrap_any(ix, p.nx), p.nx, 1, ixo);
+    if (D == 3) axis_offsets<RE>(wrap_any(iy, p.ny), p.ny, p.nx, iyo);
+    const int i_slot = (D == 3 ? (ty + R) * EX : 0) + tx + R;
+
+    const bool has_halo = tid < H;
+    int hex = 0, hey = 0;
+    if (D == 3) {
+        if (tid < R * EX) {
+            hex = tid % EX; hey = tid / EX;
+        } else if (tid < 2 * R * EX) {
+            hex = (tid - R * EX) % EX; hey = EY - R + (tid - R * EX) / EX;
+        } else {
+            const int h = tid - 2 * R * EX;
+            const int k = h % (2 * R);
+            hey = R + h / (2 * R);
+            hex = (k < R) ? k : TX + k;
+        }
+    } else {
+        hex = (tid < R) ? tid : TX + tid;
+    }
+    int hxo[2 * RE + 1], hyo[2 * RE + 1];
+    axis_offsets<RE>(wrap_any(x0 - R + hex, p.nx), p.nx, 1, hxo);
+    if (D == 3) axis_offsets<RE>(wrap_any(y0 - R + hey, p.ny), p.ny, p.nx, hyo);
+    const int h_slot = hey * EX + hex;
+    const int zero[2 * RE + 1] = {};
+    const uint32_t stI_a = smem_u32(stI) + 4u * tid;
+    const uint32_t stH_a = smem_u32(stH) + 4u * tid;
+
+    // issue the copies of slab s (own interior cell, own halo cell) and commit
+    auto stage = [&](int s) {
+        int mo[2 * RE + 1];
+        axis_offsets<RE>(wrap_near(s, nm), nm, mscale, mo);
+        const int* yi = (D == 3) ? iyo : mo;
+        const int* zi = (D == 3) ? mo : zero;
+        const uint32_t di = stI_a + 4u * static_cast<uint32_t>(ring_slot(s, NI) * Q * NT);
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+            cp_async4(di + 4u * b * NT, P.in[b] + (zi[cz + RE] + yi[cy + RE] + ixo[cx + RE]));
+        });
+        if (has_halo) {
+            const int* yh = (D == 3) ? hyo : mo;
+            const uint32_t dh = stH_a + 4u * static_cast<uint32_t>((s & 1) * Q * H);
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+                cp_async4(dh + 4u * b * H, P.in[b] + (zi[cz + RE] + yh[cy + RE] + hxo[cx + RE]));
+            });
+        }
+        cp_async_commit();
+    };
+    // psi of slab s from its staged populations
+    auto psi_slab = [&](int s) {
+        Real* dst = ring + ring_slot(s, NS) * E;
+        const Real* fi = stI + ring_slot(s, NI) * Q * NT + tid;
+        Real sum = Real(0);
+        sfor<Q>([&](auto bI) { sum += fi[decltype(bI)::value * NT]; });
+        const Real rho = Real(p.rho_bar) + sum;
+        dst[i_slot] = psi_of<LAT>(rho, p);
+        if (has_halo) {
+            const Real* fh = stH + (s & 1) * Q * H + tid;
+            Real sh = Real(0);
+            sfor<Q>([&](auto bI) { sh += fh[decltype(bI)::value * H]; });
+            dst[h_slot] = psi_of<LAT>(Real(p.rho_bar) + sh, p);
+        }
+    };
+
+    for (int s = m0 - R; s < m0 + R; ++s) {
+        stage(s);
+        cp_async_wait<0>();
+        psi_slab(s);
+    }
+    stage(m0 + R);  // psi of slab m + R is formed at iteration m from data staged one iteration earlier
+    const bool active = ix < p.nx && (D == 2 || iy < p.ny);
+    const int cell_xy = (D == 3) ? iy * p.nx + ix : ix;
+    for (int m = m0; m < m1; ++m) {
+        const bool more = m + R + 1 < m1 + R;  // the next psi slab exists
+        if (more) stage(m + R + 1);
+        if (more)
+            cp_async_wait<1>();
+        else
+            cp_async_wait<0>();
+        psi_slab(m + R);
+        __syncthreads();
+        if (active) {
+            Real f[Q];
+            const Real* fi = stI + ring_slot(m, NI) * Q * NT + tid;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                f[b] = fi[b * NT];
+            });
+            Real F[3];
+            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, p.G, F);
+            collide<LAT, COLL>(f, F, p);
+            const int c = m * mscale + cell_xy;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                P.out[b][c] = f[b];
+            });
+        }
+    }
+    cp_async_wait<0>();
 }
 
 // Deterministic block reduction of kObsWidth values (sums, last one a max).
@@ -847,16 +1065,54 @@ cudaError_t launch_fused(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB>
+template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB, int ST>
 cudaError_t launch_onepass(const LaunchArgs& a, cudaStream_t s)
 {
+    constexpr int R = Stencil<Lattice<LAT>::D, ORD>::radius;
+    constexpr size_t dyn = (ST == 2) ? sizeof(Real) * (R + 1) * Lattice<LAT>::Q * TX * TY : 0;
+    auto kern = &k_onepass<LAT, ORD, COLL, Real, TX, TY, ZC, MINB, ST>;
+    if (dyn > 48 * 1024) {
+        static bool attr_set = false;  // per instantiation
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(dyn));
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+    }
     constexpr bool k3 = Lattice<LAT>::D == 3;
     const int ntx = (a.p.nx + TX - 1) / TX;
     const int nty = k3 ? (a.p.ny + TY - 1) / TY : 1;
     const int nm = k3 ? a.p.nz : a.p.ny;
     const long long nblocks = static_cast<long long>(ntx) * nty * ((nm + ZC - 1) / ZC);
-    k_onepass<LAT, ORD, COLL, Real, TX, TY, ZC, MINB><<<static_cast<unsigned>(nblocks), TX * TY, 0, s>>>(
-        static_cast<const Real*>(a.fin), static_cast<Real*>(a.fout), a.p, ntx, nty);
+    const auto P = make_pops<Real, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
+    kern<<<static_cast<unsigned>(nblocks), TX * TY, dyn, s>>>(P, a.p, ntx, nty);
+    return cudaGetLastError();
+}
+
+template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB>
+cudaError_t launch_onepass_async(const LaunchArgs& a, cudaStream_t s)
+{
+    using L = Lattice<LAT>;
+    constexpr int R = Stencil<L::D, ORD>::radius;
+    constexpr int EX = TX + 2 * R;
+    constexpr int EY = (L::D == 3) ? TY + 2 * R : 1;
+    constexpr int H = EX * EY - TX * TY;
+    constexpr size_t dyn = sizeof(Real) * L::Q * ((R + 2) * TX * TY + 2 * H);
+    auto kern = &k_onepass_async<LAT, ORD, COLL, Real, TX, TY, ZC, MINB>;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    constexpr bool k3 = L::D == 3;
+    const int ntx = (a.p.nx + TX - 1) / TX;
+    const int nty = k3 ? (a.p.ny + TY - 1) / TY : 1;
+    const int nm = k3 ? a.p.nz : a.p.ny;
+    const long long nblocks = static_cast<long long>(ntx) * nty * ((nm + ZC - 1) / ZC);
+    const auto P = make_pops<Real, L::Q>(a.fin, a.fout, a.p.N);
+    kern<<<static_cast<unsigned>(nblocks), TX * TY, dyn, s>>>(P, a.p, ntx, nty);
     return cudaGetLastError();
 }
 
@@ -942,19 +1198,33 @@ KernelSet make_set()
         k.onepass[k.n_onepass].fn = fn;
         ++k.n_onepass;
     };
+    constexpr bool r1 = Stencil<Lattice<LAT>::D, ORD>::radius == 1;
+    constexpr bool hot = COLL == 0 && std::is_same<Real, float>::value;
     if constexpr (k3) {
-        add("onepass_32x8_z16_b2", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 2>);
-        if constexpr (COLL == 0 && std::is_same<Real, float>::value) {
-            add("onepass_32x8_z16_b3", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 3>);
-            add("onepass_32x8_z8_b3", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 8, 3>);
-            add("onepass_32x16_z16_b1", &launch_onepass<LAT, ORD, COLL, Real, 32, 16, 16, 1>);
-            if constexpr (Stencil<3, ORD>::radius == 1)
-                add("onepass_32x4_z16_b4", &launch_onepass<LAT, ORD, COLL, Real, 32, 4, 16, 4>);
+        add("onepass_32x8_z16_b2_smem", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 2, 2>);
+        if constexpr (hot) {
+            add("onepass_32x8_z16_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 4, 2>);
+            add("onepass_32x8_z16_b3_smem", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 3, 2>);
+            if constexpr (r1) {
+                add("onepass_32x8_z16_b3_reg", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 3, 1>);
+                add("onepass_32x8_z16_b5_smem", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 5, 2>);
+            }
+            add("onepass_32x8_z16_b4_regather", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 4, 0>);
+            add("onepass_async_32x8_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 32, 8, 16, 2>);
+            add("onepass_async_32x8_z32_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 32, 8, 32, 2>);
+            if constexpr (r1) {
+                add("onepass_async_32x4_z16_b4", &launch_onepass_async<LAT, ORD, COLL, Real, 32, 4, 16, 4>);
+                add("onepass_async_64x4_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 64, 4, 16, 2>);
+                add("onepass_64x4_z16_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 16, 4, 2>);
+            }
         }
     } else {
-        add("onepass_128_z16_b1", &launch_onepass<LAT, ORD, COLL, Real, 128, 1, 16, 1>);
-        if constexpr (COLL == 0 && std::is_same<Real, float>::value)
-            add("onepass_256_z16_b2", &launch_onepass<LAT, ORD, COLL, Real, 256, 1, 16, 2>);
+        add("onepass_128_z16_b2_smem", &launch_onepass<LAT, ORD, COLL, Real, 128, 1, 16, 2, 2>);
+        if constexpr (hot) {
+            add("onepass_256_z16_b3_smem", &launch_onepass<LAT, ORD, COLL, Real, 256, 1, 16, 3, 2>);
+            if constexpr (r1) add("onepass_256_z16_b3_reg", &launch_onepass<LAT, ORD, COLL, Real, 256, 1, 16, 3, 1>);
+            add("onepass_async_256_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 256, 1, 16, 2>);
+        }
     }
     k.obs = &launch_obs<LAT, ORD, Real>;
     k.probe = &launch_probe<LAT, Real>;

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "lbm_step_timed": (_I, [_P, _L, _dp, _I, ctypes.POINTER(_I)]),
     "lbm_step_kernel_name": (ctypes.c_char_p, [_P, _I]),
     "lbm_schedule_report": (_I, [_P, ctypes.c_char_p, _I]),
+    "lbm_set_schedule": (_I, [_P, ctypes.c_char_p]),
     "lbm_run_to_steady": (_I, [_P, _D, _L, _L, ctypes.POINTER(_L)]),
     "lbm_observables": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_get_fields": (_I, [_P, _dp, _dp]),
@@ -202,6 +203,10 @@ def lbm_schedule_report(ctx) -> dict:
         k, v = item.split("=")
         out[k] = v if k == "chosen" else float(v)
     return out
+
+
+def lbm_set_schedule(ctx, name: str) -> None:
+    _check(load().lbm_set_schedule(ctx, name.encode()), "lbm_set_schedule")
 
 
 def lbm_run_to_steady(ctx, tol, max_steps, check_every=1):
@@ -341,6 +346,9 @@ class Domain:
 
     def schedule_report(self):
         return lbm_schedule_report(self.ctx)
+
+    def set_schedule(self, name):
+        lbm_set_schedule(self.ctx, name)
 
     def step_timed(self, n=1):
         return lbm_step_timed(self.ctx, n)

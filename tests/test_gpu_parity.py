@@ -280,3 +280,37 @@ def test_one_pass_ragged_3d_against_oracle(lbm):
     dom.step(40)
     ref.step(40)
     assert rel_max(dom.get_f(), ref.get_f()) <= 1e-12
+
+
+@pytest.mark.parametrize("lattice,shape,stencil,precision", [
+    (1, (40, 24, 70), 4, 1),    # 3-D FP32 hot path: every compiled variant
+    (1, (21, 19, 37), 6, 1),
+    (1, (20, 16, 33), 4, 0),
+    (0, (1, 45, 300), 4, 1),
+    (0, (1, 33, 70), 10, 0),
+    (3, (1, 37, 150), 0, 1),
+])
+def test_every_schedule_variant_matches_oracle(lbm, lattice, shape, stencil, precision):
+    """Pin each schedule the autotuner could pick and compare with the oracle
+    (FP64: 1e-12; FP32: against the two-pass FP32 result to 1e-6)."""
+    nz, ny, nx = shape
+    probe = lbm.Domain(nx, ny, nz, lattice=lattice, stencil=stencil, precision=precision)
+    names = [k for k in probe.schedule_report() if k != "chosen"]
+    probe.close()
+    ref = oracle.Sim(LAT[lattice], nx, ny, nz, stencil=stencil, G=-5.0, tau=0.9)
+    ref.init_droplet(1.9, 0.15, min(nx, ny) / 4, 2.0)
+    ref.step(23)
+    f_ref = ref.get_f()
+    results = {}
+    for name in names:
+        dom = lbm.Domain(nx, ny, nz, lattice=lattice, stencil=stencil, precision=precision, tau=0.9)
+        dom.set_schedule(name)
+        dom.init_droplet(1.9, 0.15, min(nx, ny) / 4, 2.0)
+        dom.step(23)
+        results[name] = dom.get_f()
+        dom.close()
+        tol = 1e-12 if precision == 0 else 1e-5
+        assert rel_max(results[name], f_ref) <= tol, name
+    base = results["two_pass"]
+    for name, f in results.items():
+        assert np.abs(f - base).max() <= 1e-6 * np.abs(base).max(), name
