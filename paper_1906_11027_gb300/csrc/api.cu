@@ -447,7 +447,12 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     c->n_cand = 0;
     if (p->path != LBM_PATH_ONE_PASS) c->cand[c->n_cand++] = -1;
     if (p->path != LBM_PATH_TWO_PASS)
-        for (int v = 0; v < ks.n_onepass; ++v) c->cand[c->n_cand++] = v;
+        for (int v = 0; v < ks.n_onepass; ++v)
+            if (!ks.onepass[v].needs_even_nx || p->nx % 2 == 0) c->cand[c->n_cand++] = v;
+    if (c->n_cand == 0) {
+        delete c;
+        return fail(LBM_EUNSUPPORTED, "no one-pass variant applies to this domain");
+    }
     c->variant = c->cand[0];
     c->tuned = c->n_cand == 1;
 

@@ -59,8 +59,9 @@ struct LaunchArgs {
 struct StepVariant {
     const char* name;
     cudaError_t (*fn)(const LaunchArgs&, cudaStream_t);
+    bool needs_even_nx;  // two cells per thread along x
 };
-constexpr int kMaxVariants = 12;
+constexpr int kMaxVariants = 32;
 
 // One set of launchers per (lattice, stencil order, collision, precision).
 struct KernelSet {

@@ -780,6 +780,403 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     cp_async_wait<0>();
 }
 
+// Extended-tile position of halo cell h (the ring around a TX x TY tile).
+template <int D, int R, int TX, int EX, int EY>
+__device__ __forceinline__ void halo_pos(int h, int& hex, int& hey)
+{
+    if (D == 3) {
+        if (h < R * EX) {
+            hex = h % EX; hey = h / EX;
+        } else if (h < 2 * R * EX) {
+            hex = (h - R * EX) % EX; hey = EY - R + (h - R * EX) / EX;
+        } else {
+            const int g = h - 2 * R * EX;
+            const int k = g % (2 * R);
+            hey = R + g / (2 * R);
+            hex = (k < R) ? k : TX + k;
+        }
+    } else {
+        hey = 0;
+        hex = (h < R) ? h : TX + h;
+    }
+}
+
+// One-pass schedule with lookahead: iteration m first issues the loads of slab
+// m + R + 1, then collides slab m (its psi slabs were completed before the last
+// barrier), and only then forms psi of slab m + R + 1 from the loaded values, so
+// the load latency overlaps the collision.  Interior populations wait in a
+// shared-memory stash of R + 2 slabs; the psi ring has 2R + 2 slots.
+// HL = 1: the halo cells' loads also run ahead; HL = 0: only the interior ones
+// (fewer registers), the halo is gathered after the collision.
+template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB, int HL>
+__global__ void __launch_bounds__(TX * TY, MINB)
+    k_onepass_la(const __grid_constant__ Pops<Real, Lattice<LAT>::Q> P, DevParams p, int ntx, int nty)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<L::D, ORD>;
+    constexpr int D = L::D;
+    constexpr int R = S::radius;
+    constexpr int RE = L::reach;
+    constexpr int Q = L::Q;
+    constexpr int NT = TX * TY;
+    constexpr int EX = TX + 2 * R;
+    constexpr int EY = (D == 3) ? TY + 2 * R : 1;
+    constexpr int E = EX * EY;
+    constexpr int H = E - NT;
+    constexpr int NS = 2 * R + 2;
+    constexpr int NST = R + 2;
+    static_assert(H <= NT, "halo larger than the block");
+    __shared__ Real ring[NS * E];
+    extern __shared__ unsigned char dyn_smem[];
+    Real* stash = reinterpret_cast<Real*>(dyn_smem);  // [NST][Q][NT]
+
+    const int ncol = ntx * nty;
+    const int col = blockIdx.x % ncol;
+    const int chunk = blockIdx.x / ncol;
+    const int x0 = (col % ntx) * TX;
+    const int y0 = (D == 3) ? (col / ntx) * TY : 0;
+    const int nm = (D == 3) ? p.nz : p.ny;
+    const int m0 = chunk * ZC;
+    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const int mscale = (D == 3) ? p.nx * p.ny : p.nx;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+
+    const int ix = x0 + tx, iy = y0 + ty;
+    int ixo[2 * RE + 1], iyo[2 * RE + 1];
+    axis_offsets<RE>(wrap_any(ix, p.nx), p.nx, 1, ixo);
+    if (D == 3) axis_offsets<RE>(wrap_any(iy, p.ny), p.ny, p.nx, iyo);
+    const int i_slot = (D == 3 ? (ty + R) * EX : 0) + tx + R;
+    const bool has_halo = tid < H;
+    int hex, hey;
+    halo_pos<D, R, TX, EX, EY>(has_halo ? tid : 0, hex, hey);
+    int hxo[2 * RE + 1], hyo[2 * RE + 1];
+    axis_offsets<RE>(wrap_any(x0 - R + hex, p.nx), p.nx, 1, hxo);
+    if (D == 3) axis_offsets<RE>(wrap_any(y0 - R + hey, p.ny), p.ny, p.nx, hyo);
+    const int h_slot = hey * EX + hex;
+    const int zero[2 * RE + 1] = {};
+
+    Real fl[Q], hl[Q];
+    auto load_halo = [&](int m) {
+        int mo[2 * RE + 1];
+        axis_offsets<RE>(wrap_near(m, nm), nm, mscale, mo);
+        if (D == 3) {
+            if (has_halo) gather_off<LAT, Real, RE>(P, hxo, hyo, mo, hl);
+        } else {
+            if (has_halo) gather_off<LAT, Real, RE>(P, hxo, mo, zero, hl);
+        }
+    };
+    auto load_slab = [&](int m) {
+        int mo[2 * RE + 1];
+        axis_offsets<RE>(wrap_near(m, nm), nm, mscale, mo);
+        if (D == 3)
+            gather_off<LAT, Real, RE>(P, ixo, iyo, mo, fl);
+        else
+            gather_off<LAT, Real, RE>(P, ixo, mo, zero, fl);
+        if (HL) load_halo(m);
+    };
+    auto finish_slab = [&](int m) {
+        if (!HL) load_halo(m);
+        Real* dst = ring + ring_slot(m, NS) * E;
+        Real sum = Real(0);
+        sfor<Q>([&](auto bI) { sum += fl[decltype(bI)::value]; });
+        dst[i_slot] = psi_of<LAT>(std::is_same<Real, float>::value ? Real(p.rho_bar) + sum : sum, p);
+        Real* st = stash + ring_slot(m, NST) * (Q * NT) + tid;
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            st[b * NT] = fl[b];
+        });
+        if (has_halo) {
+            Real sh = Real(0);
+            sfor<Q>([&](auto bI) { sh += hl[decltype(bI)::value]; });
+            dst[h_slot] = psi_of<LAT>(std::is_same<Real, float>::value ? Real(p.rho_bar) + sh : sh, p);
+        }
+    };
+
+    for (int m = m0 - R; m <= m0 + R; ++m) {
+        load_slab(m);
+        finish_slab(m);
+    }
+    __syncthreads();
+    const bool active = ix < p.nx && (D == 2 || iy < p.ny);
+    const int cell_xy = (D == 3) ? iy * p.nx + ix : ix;
+    for (int m = m0; m < m1; ++m) {
+        const bool ahead = m + 1 < m1;  // psi of slab m + R + 1 is needed
+        if (ahead) load_slab(m + R + 1);
+        if (active) {
+            Real f[Q];
+            const Real* st = stash + ring_slot(m, NST) * (Q * NT) + tid;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                f[b] = st[b * NT];
+            });
+            Real F[3];
+            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, p.G, F);
+            collide<LAT, COLL>(f, F, p);
+            const int c = m * mscale + cell_xy;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                P.out[b][c] = f[b];
+            });
+        }
+        if (ahead) finish_slab(m + R + 1);
+        __syncthreads();
+    }
+}
+
+// ---- one-pass schedule, two cells per thread, packed FP32 ---------------------
+// FP32 BGK only.  A thread owns the x-adjacent cells (x, x+1), x even, so the
+// directions with c_x = 0 are gathered with one 8-byte load and every store is
+// one 8-byte store (longer DRAM row segments: a warp covers 64 cells), and all
+// per-cell arithmetic runs on float2 pairs with the packed FP32 instructions
+// (__ffma2_rn / __fadd2_rn / __fmul2_rn).  Needs an even nx.
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, p2(-1.f), a); }
+
+// c . v for a compile-time integer vector c (components in -3..3)
+template <int CX, int CY, int CZ>
+__device__ __forceinline__ float2 cdot2(float2 vx, float2 vy, float2 vz)
+{
+    float2 r = p2(0.f);
+    bool any = false;
+    auto acc = [&](int c, float2 v) {
+        if (c == 0) return;
+        if (!any) {
+            r = (c == 1) ? v : mul2(p2(float(c)), v);
+            any = true;
+        } else if (c == 1) {
+            r = add2(r, v);
+        } else if (c == -1) {
+            r = sub2(r, v);
+        } else {
+            r = fma2(p2(float(c)), v, r);
+        }
+    };
+    acc(CX, vx);
+    acc(CY, vy);
+    acc(CZ, vz);
+    return r;
+}
+
+template <int LAT>
+__device__ __forceinline__ void collide2_bgk(float2 (&f)[Lattice<LAT>::Q], const float2 (&F)[3], const DevParams& p)
+{
+    using L = Lattice<LAT>;
+    constexpr int Q = L::Q;
+    float2 s = f[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
+    sfor<(Q - 1) / 2>([&](auto kI) {
+        constexpr int b = 1 + 2 * decltype(kI)::value;
+        constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+        s = add2(s, add2(f[b], f[b + 1]));
+        const float2 d = sub2(f[b], f[b + 1]);
+        if (cx == 1) jx = add2(jx, d); else if (cx == -1) jx = sub2(jx, d); else if (cx != 0) jx = fma2(p2(float(cx)), d, jx);
+        if (cy == 1) jy = add2(jy, d); else if (cy == -1) jy = sub2(jy, d); else if (cy != 0) jy = fma2(p2(float(cy)), d, jy);
+        if (cz == 1) jz = add2(jz, d); else if (cz == -1) jz = sub2(jz, d); else if (cz != 0) jz = fma2(p2(float(cz)), d, jz);
+    });
+    const float2 rho = add2(p2(float(p.rho_bar)), s);
+    const float2 inv_rho = make_float2(1.f / rho.x, 1.f / rho.y);
+    const float2 ux = mul2(fma2(p2(0.5f), F[0], jx), inv_rho);
+    const float2 uy = mul2(fma2(p2(0.5f), F[1], jy), inv_rho);
+    const float2 uz = mul2(fma2(p2(0.5f), F[2], jz), inv_rho);
+    constexpr double cs2 = L::cs2;
+    const float2 usq = mul2(fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))), p2(float(0.5 / cs2)));
+    const float2 uF = fma2(ux, F[0], fma2(uy, F[1], mul2(uz, F[2])));
+    const float2 omega = p2(float(p.omega));
+    const float2 pref = p2(float(p.pref));
+    const float2 orho = mul2(omega, rho);
+    // A0 = omega s - omega rho usq - pref uF / cs2
+    const float2 A0 = fma2(mul2(pref, p2(float(-1.0 / cs2))), uF, fma2(orho, sub2(p2(0.f), usq), mul2(omega, s)));
+    const float2 ic2 = p2(float(1.0 / cs2)), ic4 = p2(float(1.0 / (cs2 * cs2)));
+    const float2 Px = mul2(fma2(orho, ux, mul2(pref, F[0])), ic2);
+    const float2 Py = mul2(fma2(orho, uy, mul2(pref, F[1])), ic2);
+    const float2 Pz = mul2(fma2(orho, uz, mul2(pref, F[2])), ic2);
+    const float2 h = mul2(p2(0.5f), orho);
+    const float2 Vx = mul2(fma2(h, ux, mul2(pref, F[0])), ic4);
+    const float2 Vy = mul2(fma2(h, uy, mul2(pref, F[1])), ic4);
+    const float2 Vz = mul2(fma2(h, uz, mul2(pref, F[2])), ic4);
+    const float2 om1 = p2(float(1.0 - p.omega));
+    {
+        constexpr double w0 = L::T.w[0];
+        f[0] = fma2(f[0], om1, mul2(p2(float(w0)), A0));
+    }
+    sfor<(Q - 1) / 2>([&](auto kI) {
+        constexpr int b = 1 + 2 * decltype(kI)::value;
+        constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+        constexpr double wb = L::T.w[b];
+        const float2 cu = cdot2<cx, cy, cz>(ux, uy, uz);
+        const float2 cV = cdot2<cx, cy, cz>(Vx, Vy, Vz);
+        const float2 cP = cdot2<cx, cy, cz>(Px, Py, Pz);
+        const float2 ev = fma2(cu, cV, A0);
+        f[b] = fma2(f[b], om1, mul2(p2(float(wb)), add2(ev, cP)));
+        f[b + 1] = fma2(f[b + 1], om1, mul2(p2(float(wb)), sub2(ev, cP)));
+    });
+}
+
+template <int LAT, int ORD, int TX2, int TY, int ZC, int MINB, int ST>
+__global__ void __launch_bounds__(TX2 * TY, MINB)
+    k_onepass_x2(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, int ntx, int nty)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<L::D, ORD>;
+    constexpr int D = L::D;
+    constexpr int R = S::radius;
+    constexpr int RE = L::reach;
+    constexpr int Q = L::Q;
+    constexpr int NT = TX2 * TY;
+    constexpr int TX = 2 * TX2;
+    constexpr int EX = TX + 2 * R;
+    constexpr int EY = (D == 3) ? TY + 2 * R : 1;
+    constexpr int E = EX * EY;
+    constexpr int H = E - TX * TY;
+    constexpr int NS = 2 * R + 2;
+    constexpr int NST = R + 1;
+    static_assert(H <= 2 * NT, "halo larger than two cells per thread");
+    static_assert(ST == 2 || (ST == 1 && R == 1), "stash in shared memory, or registers for radius 1");
+    __shared__ float ring[NS * E];
+    extern __shared__ unsigned char dyn_smem[];
+    float2* stash = reinterpret_cast<float2*>(dyn_smem);  // [NST][Q][NT] when ST == 2
+
+    const int ncol = ntx * nty;
+    const int col = blockIdx.x % ncol;
+    const int chunk = blockIdx.x / ncol;
+    const int x0 = (col % ntx) * TX;
+    const int y0 = (D == 3) ? (col / ntx) * TY : 0;
+    const int nm = (D == 3) ? p.nz : p.ny;
+    const int m0 = chunk * ZC;
+    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const int mscale = (D == 3) ? p.nx * p.ny : p.nx;
+    const int tid = threadIdx.x;
+    const int tx2 = tid % TX2, ty = tid / TX2;
+
+    // interior pair (ix, ix + 1), ix even
+    const int ix = x0 + 2 * tx2, iy = y0 + ty;
+    const int ixw = wrap_any(ix, p.nx);
+    int xa[2 * RE + 1], xb[2 * RE + 1], iyo[2 * RE + 1];
+    axis_offsets<RE>(ixw, p.nx, 1, xa);
+    axis_offsets<RE>(ixw + 1 < p.nx ? ixw + 1 : 0, p.nx, 1, xb);
+    if (D == 3) axis_offsets<RE>(wrap_any(iy, p.ny), p.ny, p.nx, iyo);
+    const int i_pos = (D == 3 ? (ty + R) * EX : 0) + 2 * tx2 + R;
+
+    // up to two halo cells: h = tid and h = tid + NT
+    int hx0[2 * RE + 1], hy0[2 * RE + 1], hx1[2 * RE + 1], hy1[2 * RE + 1];
+    int hpos0 = 0, hpos1 = 0;
+    const bool h0 = tid < H, h1 = tid + NT < H;
+    {
+        int ex, ey;
+        halo_pos<D, R, TX, EX, EY>(h0 ? tid : 0, ex, ey);
+        axis_offsets<RE>(wrap_any(x0 - R + ex, p.nx), p.nx, 1, hx0);
+        if (D == 3) axis_offsets<RE>(wrap_any(y0 - R + ey, p.ny), p.ny, p.nx, hy0);
+        hpos0 = ey * EX + ex;
+        halo_pos<D, R, TX, EX, EY>(h1 ? tid + NT : 0, ex, ey);
+        axis_offsets<RE>(wrap_any(x0 - R + ex, p.nx), p.nx, 1, hx1);
+        if (D == 3) axis_offsets<RE>(wrap_any(y0 - R + ey, p.ny), p.ny, p.nx, hy1);
+        hpos1 = ey * EX + ex;
+    }
+    const int zero[2 * RE + 1] = {};
+
+    float2 fcur[Q], fnxt[Q];
+
+    auto halo_psi = [&](const int (&hx)[2 * RE + 1], const int* yo, const int* zo, float* dst) {
+        float sum = 0.f;
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+            sum += __ldg(P.in[b] + (zo[cz + RE] + yo[cy + RE] + hx[cx + RE]));
+        });
+        *dst = psi_exp(float(p.rho_bar) + sum);
+    };
+
+    auto psi_slab = [&](int m) {
+        int mo[2 * RE + 1];
+        axis_offsets<RE>(wrap_near(m, nm), nm, mscale, mo);
+        const int* yi = (D == 3) ? iyo : mo;
+        const int* zi = (D == 3) ? mo : zero;
+        float* dst = ring + ring_slot(m, NS) * E;
+        float2 sum = p2(0.f);
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+            const int base = zi[cz + RE] + yi[cy + RE];
+            if (cx == 0) {
+                fnxt[b] = __ldg(reinterpret_cast<const float2*>(P.in[b] + (base + xa[RE])));
+            } else {
+                fnxt[b] = make_float2(__ldg(P.in[b] + (base + xa[cx + RE])), __ldg(P.in[b] + (base + xb[cx + RE])));
+            }
+            sum = add2(sum, fnxt[b]);
+        });
+        const float2 rho = add2(p2(float(p.rho_bar)), sum);
+        dst[i_pos] = psi_exp(rho.x);
+        dst[i_pos + 1] = psi_exp(rho.y);
+        if (ST == 2) {
+            float2* st = stash + static_cast<unsigned>(m + 4 * NST) % NST * (Q * NT) + tid;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                st[b * NT] = fnxt[b];
+            });
+        }
+        const int* yh0 = (D == 3) ? hy0 : mo;
+        const int* yh1 = (D == 3) ? hy1 : mo;
+        if (h0) halo_psi(hx0, yh0, zi, dst + hpos0);
+        if (h1) halo_psi(hx1, yh1, zi, dst + hpos1);
+    };
+
+    for (int m = m0 - R; m < m0 + R; ++m) {
+        psi_slab(m);
+        if (ST == 1 && m == m0 + R - 1) {
+#pragma unroll
+            for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+        }
+    }
+    const bool active = ix < p.nx && (D == 2 || iy < p.ny);
+    const int cell_xy = (D == 3) ? iy * p.nx + ix : ix;
+    for (int m = m0; m < m1; ++m) {
+        psi_slab(m + R);
+        __syncthreads();
+        if (active) {
+            if (ST == 2) {
+                const float2* st = stash + static_cast<unsigned>(m + 4 * NST) % NST * (Q * NT) + tid;
+                sfor<Q>([&](auto bI) {
+                    constexpr int b = decltype(bI)::value;
+                    fcur[b] = st[b * NT];
+                });
+            }
+            // force (Eq. 1) of both cells from the psi ring, opposite vectors paired
+            const float* base[2 * R + 1];
+#pragma unroll
+            for (int k = 0; k < 2 * R + 1; ++k) base[k] = ring + ring_slot(m - R + k, NS) * E + i_pos;
+            float2 ax = p2(0.f), ay = p2(0.f), az = p2(0.f);
+            sfor<S::n / 2>([&](auto kI) {
+                constexpr int a = 2 * decltype(kI)::value;
+                constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1], ez = S::T.v[a][2];
+                constexpr int dm = (D == 3) ? ez : ey;
+                constexpr int dq = (D == 3) ? ey : 0;
+                constexpr double wt = S::T.w[a] * L::cs2;
+                const float* pp = base[dm + R] + dq * EX + ex;
+                const float* pm = base[R - dm] - dq * EX - ex;
+                const float2 d = sub2(make_float2(pp[0], pp[1]), make_float2(pm[0], pm[1]));
+                if (ex != 0) ax = fma2(p2(float(wt * ex)), d, ax);
+                if (ey != 0) ay = fma2(p2(float(wt * ey)), d, ay);
+                if (ez != 0) az = fma2(p2(float(wt * ez)), d, az);
+            });
+            const float2 gp = mul2(p2(float(-p.G)), make_float2(base[R][0], base[R][1]));
+            const float2 F[3] = {mul2(gp, ax), mul2(gp, ay), mul2(gp, az)};
+            collide2_bgk<LAT>(fcur, F, p);
+            const int c = m * mscale + cell_xy;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                *reinterpret_cast<float2*>(P.out[b] + c) = fcur[b];
+            });
+        }
+        if (ST == 1) {
+#pragma unroll
+            for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+        }
+    }
+}
+
 // Deterministic block reduction of kObsWidth values (sums, last one a max).
 __device__ __forceinline__ void block_reduce_obs(double (&v)[kObsWidth], double* out)
 {
@@ -1116,6 +1513,59 @@ cudaError_t launch_onepass_async(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB, int HL>
+cudaError_t launch_onepass_la(const LaunchArgs& a, cudaStream_t s)
+{
+    using L = Lattice<LAT>;
+    constexpr int R = Stencil<L::D, ORD>::radius;
+    constexpr size_t dyn = sizeof(Real) * (R + 2) * L::Q * TX * TY;
+    auto kern = &k_onepass_la<LAT, ORD, COLL, Real, TX, TY, ZC, MINB, HL>;
+    if (dyn > 48 * 1024) {
+        static bool attr_set = false;  // per instantiation
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(dyn));
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+    }
+    constexpr bool k3 = L::D == 3;
+    const int ntx = (a.p.nx + TX - 1) / TX;
+    const int nty = k3 ? (a.p.ny + TY - 1) / TY : 1;
+    const int nm = k3 ? a.p.nz : a.p.ny;
+    const long long nblocks = static_cast<long long>(ntx) * nty * ((nm + ZC - 1) / ZC);
+    const auto P = make_pops<Real, L::Q>(a.fin, a.fout, a.p.N);
+    kern<<<static_cast<unsigned>(nblocks), TX * TY, dyn, s>>>(P, a.p, ntx, nty);
+    return cudaGetLastError();
+}
+
+template <int LAT, int ORD, int TX2, int TY, int ZC, int MINB, int ST>
+cudaError_t launch_onepass_x2(const LaunchArgs& a, cudaStream_t s)
+{
+    using L = Lattice<LAT>;
+    constexpr int R = Stencil<L::D, ORD>::radius;
+    constexpr size_t dyn = (ST == 2) ? sizeof(float2) * (R + 1) * L::Q * TX2 * TY : 0;
+    auto kern = &k_onepass_x2<LAT, ORD, TX2, TY, ZC, MINB, ST>;
+    if (dyn > 48 * 1024) {
+        static bool attr_set = false;  // per instantiation
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(dyn));
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+    }
+    constexpr bool k3 = L::D == 3;
+    constexpr int TX = 2 * TX2;
+    const int ntx = (a.p.nx + TX - 1) / TX;
+    const int nty = k3 ? (a.p.ny + TY - 1) / TY : 1;
+    const int nm = k3 ? a.p.nz : a.p.ny;
+    const long long nblocks = static_cast<long long>(ntx) * nty * ((nm + ZC - 1) / ZC);
+    const auto P = make_pops<float, L::Q>(a.fin, a.fout, a.p.N);
+    kern<<<static_cast<unsigned>(nblocks), TX2 * TY, dyn, s>>>(P, a.p, ntx, nty);
+    return cudaGetLastError();
+}
+
 template <int LAT, int ORD, class Real>
 cudaError_t launch_obs(const LaunchArgs& a, cudaStream_t s, int* nblocks)
 {
@@ -1193,9 +1643,11 @@ KernelSet make_set()
     // One-pass variants timed by the autotuner: tile TX x TY (2-D: TX), chunk of
     // ZC slabs, at least MINB resident blocks per SM (a register cap).
     k.n_onepass = 0;
-    auto add = [&k](const char* name, cudaError_t (*fn)(const LaunchArgs&, cudaStream_t)) {
+    auto add = [&k](const char* name, cudaError_t (*fn)(const LaunchArgs&, cudaStream_t), bool even_nx = false) {
+        if (k.n_onepass >= kMaxVariants) return;  // table full: later variants are not offered
         k.onepass[k.n_onepass].name = name;
         k.onepass[k.n_onepass].fn = fn;
+        k.onepass[k.n_onepass].needs_even_nx = even_nx;
         ++k.n_onepass;
     };
     constexpr bool r1 = Stencil<Lattice<LAT>::D, ORD>::radius == 1;
@@ -1207,15 +1659,26 @@ KernelSet make_set()
             add("onepass_32x8_z16_b3_smem", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 3, 2>);
             if constexpr (r1) {
                 add("onepass_32x8_z16_b3_reg", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 3, 1>);
-                add("onepass_32x8_z16_b5_smem", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 5, 2>);
-            }
+                }
             add("onepass_32x8_z16_b4_regather", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 4, 0>);
             add("onepass_async_32x8_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 32, 8, 16, 2>);
             add("onepass_async_32x8_z32_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 32, 8, 32, 2>);
             if constexpr (r1) {
-                add("onepass_async_32x4_z16_b4", &launch_onepass_async<LAT, ORD, COLL, Real, 32, 4, 16, 4>);
                 add("onepass_async_64x4_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 64, 4, 16, 2>);
                 add("onepass_64x4_z16_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 16, 4, 2>);
+                add("onepass_x2_64x8_z16_b2_reg", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 1>, true);
+                add("onepass_128x4_z16_b2_smem", &launch_onepass<LAT, ORD, COLL, Real, 128, 4, 16, 2, 2>);
+                add("onepass_64x4_z8_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 8, 4, 2>);
+                add("onepass_64x4_z32_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 32, 4, 2>);
+                add("onepass_la_64x4_z16_b2", &launch_onepass_la<LAT, ORD, COLL, Real, 64, 4, 16, 2, 1>);
+                add("onepass_lai_64x4_z16_b3", &launch_onepass_la<LAT, ORD, COLL, Real, 64, 4, 16, 3, 0>);
+                add("onepass_lai_64x4_z16_b4", &launch_onepass_la<LAT, ORD, COLL, Real, 64, 4, 16, 4, 0>);
+                add("onepass_lai_64x4_z32_b3", &launch_onepass_la<LAT, ORD, COLL, Real, 64, 4, 32, 3, 0>);
+            }
+            add("onepass_la_32x8_z16_b2", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 2, 1>);
+            add("onepass_lai_32x8_z16_b3", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 3, 0>);
+            add("onepass_x2_64x8_z16_b2_smem", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 2>, true);
+            if constexpr (r1) {
             }
         }
     } else {
@@ -1224,6 +1687,7 @@ KernelSet make_set()
             add("onepass_256_z16_b3_smem", &launch_onepass<LAT, ORD, COLL, Real, 256, 1, 16, 3, 2>);
             if constexpr (r1) add("onepass_256_z16_b3_reg", &launch_onepass<LAT, ORD, COLL, Real, 256, 1, 16, 3, 1>);
             add("onepass_async_256_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 256, 1, 16, 2>);
+            add("onepass_x2_256_z16_b2_smem", &launch_onepass_x2<LAT, ORD, 128, 1, 16, 2, 2>, true);
         }
     }
     k.obs = &launch_obs<LAT, ORD, Real>;

@@ -196,8 +196,8 @@ def lbm_step_kernel_name(ctx, i: int) -> str:
 
 def lbm_schedule_report(ctx) -> dict:
     """{'chosen': name, name: ms per step, ...} of the step-schedule autotuner."""
-    buf = ctypes.create_string_buffer(1024)
-    _check(load().lbm_schedule_report(ctx, buf, 1024), "lbm_schedule_report")
+    buf = ctypes.create_string_buffer(4096)
+    _check(load().lbm_schedule_report(ctx, buf, 4096), "lbm_schedule_report")
     out = {}
     for item in buf.value.decode().split(";"):
         k, v = item.split("=")

@@ -2,7 +2,7 @@
 profiler can capture individual kernels.
 
     python -m paper_1906_11027_gb300.profile_case --lattice d3q19 --n 128 --steps 6 \
-        [--precision fp32|fp64] [--stencil 4] [--path auto|two|one]
+        [--precision fp32|fp64] [--stencil 4] [--path auto|two|one] [--schedule NAME]
 """
 import argparse
 import os
@@ -24,12 +24,15 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--stencil", type=int, default=0)
     ap.add_argument("--path", choices=sorted(PATHS), default="auto")
+    ap.add_argument("--schedule", default=None, help="pin a schedule by name (lbm_schedule_report)")
     a = ap.parse_args()
     lat = LATTICES[a.lattice]
     nz = a.n if lat == lbm.LBM_D3Q19 else 1
     dom = lbm.Domain(a.n, a.n, nz, lattice=lat, stencil=a.stencil,
                      precision=lbm.LBM_FP32_SHIFTED if a.precision == "fp32" else lbm.LBM_FP64,
                      path=PATHS[a.path])
+    if a.schedule:
+        dom.set_schedule(a.schedule)
     dom.init_droplet(2.0, 0.15, 0.15 * a.n, 2.0)
     for _ in range(a.steps):  # one call per step: no graph replay
         dom.step(1)

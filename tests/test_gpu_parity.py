@@ -311,6 +311,8 @@ def test_every_schedule_variant_matches_oracle(lbm, lattice, shape, stencil, pre
         dom.close()
         tol = 1e-12 if precision == 0 else 1e-5
         assert rel_max(results[name], f_ref) <= tol, name
+    # FP32 variants order their float operations differently (packed pairs,
+    # regrouped sums), so they agree with each other within the FP32 budget
     base = results["two_pass"]
     for name, f in results.items():
-        assert np.abs(f - base).max() <= 1e-6 * np.abs(base).max(), name
+        assert np.abs(f - base).max() <= (1e-13 if precision == 0 else 1e-5) * np.abs(base).max(), name
