@@ -319,6 +319,83 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_sweep(args):
+    """Batched FP32 sweep (one persistent-kernel CUDA graph for all domains) against
+    plain FP64 one-domain-per-launch runs of the same domains, both to steady state."""
+    import torch
+    from paper_1906_11027_gb300 import inputs, lbm
+
+    lbm.load()
+    doms = inputs.sweep_domains(args.sweep_domains)
+    cells = sum(d["nx"] * d["ny"] for d in doms)
+    torch.cuda.synchronize()
+    # warm the kernels (module load) outside the timed regions
+    w = lbm.Batch(doms[:2], precision=lbm.LBM_FP32_SHIFTED)
+    w.step(4)
+    w.close()
+    K = 100
+    t0 = time.perf_counter()
+    b = lbm.Batch(doms, precision=lbm.LBM_FP32_SHIFTED)
+    steps32, obs32, ok32 = b.run_to_steady(1e-10, args.sweep_max_steps, K)
+    # precision policy: a steady current below FP32's velocity resolution is
+    # re-converged in FP64, continued from the FP32 state
+    tiny = [i for i, o in enumerate(obs32) if np.isfinite(o["max_u"]) and o["max_u"] < args.fp64_below]
+    if tiny:
+        b64 = lbm.Batch([doms[i] for i in tiny], precision=lbm.LBM_FP64)
+        for j, i in enumerate(tiny):
+            b64.set_f(j, b.get_f(i))
+        s64, o64, _ = b64.run_to_steady(1e-10, args.sweep_max_steps, K)
+        for j, i in enumerate(tiny):
+            steps32[i] += s64[j]
+            obs32[i] = o64[j]
+        b64.close()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    b.close()
+    t0 = time.perf_counter()
+    steps64, obs64 = [], []
+    for d in doms:
+        dom = lbm.Domain(d["nx"], d["ny"], G=d["G"], tau=d["tau"], stencil=d["stencil"], precision=lbm.LBM_FP64)
+        dom.init_droplet(d["rho_l"], d["rho_g"], d["R"], d["width"])
+        try:
+            s, ok = dom.run_to_steady(1e-10, args.sweep_max_steps, K)
+            o = dom.observables()
+        except lbm.LbmError as e:  # the BGK model diverges for some (G, tau) pairs
+            if e.code != lbm.LBM_ENONFINITE:
+                raise
+            s, o = args.sweep_max_steps, {"max_u": float("inf")}
+        steps64.append(s)
+        obs64.append(o)
+        dom.close()
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    finite = [i for i in range(len(doms)) if np.isfinite(obs64[i]["max_u"]) and np.isfinite(obs32[i]["max_u"])]
+    diverged = {"fp64": sum(1 for o in obs64 if not np.isfinite(o["max_u"])),
+                "batched_fp32": sum(1 for o in obs32 if not np.isfinite(o["max_u"]))}
+    ratio = [abs(obs32[i]["max_u"] / obs64[i]["max_u"] - 1.0) for i in finite] or [float("nan")]
+    line = {
+        "metric": "sweep_time_to_steady_s", "value": round(t_batch, 3), "unit": "s", "higher_is_better": False,
+        "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "d2q9_sweep", "domains": len(doms), "cells": cells, "seed": inputs.SWEEP_SEED,
+                   "rule": "|max|u|(t) - max|u|(t-100)| / 100 < 1e-10 (FP32 adds the floor 1e-6 max|u|/100), "
+                           "checked every 100 steps in both arms",
+                   "fp64_below": args.fp64_below, "promoted_to_fp64": len(tiny),
+                   "max_steps": args.sweep_max_steps},
+        "baseline_fp64_one_domain_per_launch_s": round(t_fp64, 3),
+        "speedup": round(t_fp64 / t_batch, 2),
+        "converged": {"batched_fp32": bool(ok32), "fp64": sum(1 for s in steps64 if s < args.sweep_max_steps)},
+        "steps": {"batched_fp32_total": int(sum(steps32)), "fp64_total": int(sum(steps64))},
+        "diverged": diverged,
+        "per_domain": [[d["nx"], round(d["G"], 3), d["tau"], d["stencil"], round(d["R"], 1), int(steps32[i]),
+                        int(steps64[i]), float("%.4g" % obs32[i]["max_u"]), float("%.4g" % obs64[i]["max_u"])]
+                       for i, d in enumerate(doms)] if args.sweep_details else None,
+        "max_u_rel_diff": {"max": round(max(ratio), 4), "median": round(float(np.median(ratio)), 4),
+                           "within_5pct": sum(1 for r in ratio if r <= 0.05), "compared": len(finite)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -328,10 +405,18 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d3q19_256_fp32")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--path", choices=["auto", "two", "one"], default="auto")
+    ap.add_argument("--sweep", action="store_true", help="time the batched sweep instead of the step")
+    ap.add_argument("--sweep-domains", type=int, default=64)
+    ap.add_argument("--sweep-max-steps", type=int, default=200000)
+    ap.add_argument("--sweep-details", action="store_true")
+    ap.add_argument("--fp64-below", type=float, default=1e-6,
+                    help="steady max|u| under which an FP32 domain is re-converged in FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.sweep:
+        return run_sweep(args)
     world, rank, local = dist_setup(args)
     try:
         if args.impl == "reference":

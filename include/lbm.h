@@ -203,6 +203,44 @@ int lbm_load(lbm_ctx* ctx, const char* path);
  * one write and one read of psi). */
 double lbm_bytes_per_update(const lbm_ctx* ctx);
 
+/* ---- batched sweep of independent 2-D domains --------------------------------- */
+
+/* A batch advances n independent periodic D2Q9 domains (each with its own size,
+ * G, tau and force-stencil order; exp psi, BGK, one precision for all) with one
+ * persistent kernel per step over a work list of (domain, tile, row chunk)
+ * items, inside a CUDA graph that also checks every domain for steady state;
+ * converged domains retire from the work list (the parameter study of the
+ * paper's Sec. 3, run as one job). */
+typedef struct lbm_batch lbm_batch;
+
+/* ps[d]: lattice = LBM_D2Q9, psi = LBM_PSI_EXP, collision = LBM_BGK, nx, ny >= 8,
+ * nz = 1, stencil 0/4/6/8/10, G, tau; precision, stream and allocator are taken
+ * from ps[0] (all precisions equal).  init[4d .. 4d+3] = rho_l, rho_g, R, width of
+ * domain d's centred tanh droplet (as lbm_init_droplet). */
+int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch** out);
+int lbm_batch_destroy(lbm_batch* b);
+
+/* n steps of every active domain, without checks (asynchronous). */
+int lbm_batch_step(lbm_batch* b, int64_t n);
+
+/* Replays blocks of check_every (even) steps until every domain satisfies
+ * |max|u|(t) - max|u|(t - K)| / K < tol (FP32 adds the floor 1e-6 max|u| / K) or
+ * max_steps.  steps_per_domain[d] (may be NULL) = steps domain d took before it
+ * retired; obs_per_domain[d] (may be NULL) = its observables (rho_l, rho_g, dp,
+ * max_u, mean_u, mass, mom, step; thickness 0).  A domain whose fields become
+ * non-finite (the BGK pseudo-potential model diverges for some strong-G, small-tau
+ * pairs) retires at that check with max_u = +inf.  LBM_ENOTCONVERGED if domains
+ * remain active at max_steps (outputs still filled). */
+int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t check_every,
+                            int64_t* steps_per_domain, lbm_obs* obs_per_domain);
+int lbm_batch_observables(lbm_batch* b, lbm_obs* obs_per_domain);
+
+/* Pre-collision populations of domain d in double, [9][ny][nx], from / to host
+ * arrays (set_populations writes the buffer that holds the domain's state, e.g.
+ * to continue in FP64 a domain converged in FP32). */
+int lbm_batch_get_populations(lbm_batch* b, int d, double* f_host);
+int lbm_batch_set_populations(lbm_batch* b, int d, const double* f_host);
+
 /* Mass and momentum totals of a population buffer, computed without allocating
  * anything.  The paper has no counterpart: this serves callers that cannot
  * allocate device memory at the moment they need the totals, such as an

@@ -1,0 +1,813 @@
+// batch.cu -- many independent 2-D D2Q9 domains (uneven sizes, each with its own
+// G, tau, stencil order and initial droplet) advanced together by one persistent
+// kernel per step, captured in a CUDA graph together with a per-domain steady
+// check; converged domains retire and drop out of the work list.
+//
+// Work item = (domain, tile of TX cells along x, chunk of ZC rows along y).  Each
+// item runs the one-pass march of the single-domain kernels: psi of the tile and
+// its halo is formed one row ahead into a shared-memory ring, the populations
+// wait in a shared-memory stash, then force (Eq. 1), Guo-forced BGK collision
+// (Eqs. 3-4) and the pull-streamed store.  The item count lives in device
+// memory, so a captured graph stays valid while the list shrinks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kBTX = 64;   // tile width (threads per CTA)
+constexpr int kBZC = 16;   // rows per chunk
+constexpr int kBMaxR = 3;  // largest stencil radius (10th order)
+constexpr int kBNS = 2 * kBMaxR + 2;
+constexpr int kBEX = kBTX + 2 * kBMaxR;
+constexpr int kQ9 = 9;
+
+struct BatchDom {
+    int nx, ny, order, ntx, nch, active;
+    long long off;   // element offset of the domain in each population pool
+    double G, omega, pref, rho_bar;
+};
+
+__device__ __forceinline__ DevParams dom_params(const BatchDom& d)
+{
+    DevParams p{};
+    p.nx = d.nx;
+    p.ny = d.ny;
+    p.nz = 1;
+    p.N = static_cast<long long>(d.nx) * d.ny;
+    p.G = d.G;
+    p.omega = d.omega;
+    p.pref = d.pref;
+    p.rho_bar = d.rho_bar;
+    p.psi_kind = 0;
+    return p;
+}
+
+// One (tile, chunk) of one domain: the 2-D one-pass march with a shared-memory
+// stash.  ring: [NS][EX] psi, stash: [R + 1][Q][TX] populations.
+template <int ORD, class Real>
+__device__ void batch_item(const Real* __restrict__ A, Real* __restrict__ Bo, const DevParams& p, int x0, int m0,
+                           Real* ring, Real* stash)
+{
+    using L = Lattice<kLatD2Q9>;
+    using S = Stencil<2, ORD>;
+    constexpr int R = S::radius;
+    constexpr int RE = 1;
+    constexpr int Q = kQ9;
+    constexpr int TX = kBTX;
+    constexpr int EX = TX + 2 * R;
+    constexpr int E = EX;
+    constexpr int NS = 2 * R + 2;
+    constexpr int NST = R + 1;
+    Pops<Real, Q> P;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+        P.in[b] = A + static_cast<long long>(b) * p.N;
+        P.out[b] = Bo + static_cast<long long>(b) * p.N;
+    }
+    const int nm = p.ny;
+    const int m1 = (m0 + kBZC < nm) ? m0 + kBZC : nm;
+    const int tid = threadIdx.x;
+    const int ix = x0 + tid;
+    int ixo[2 * RE + 1];
+    axis_offsets<RE>(wrap_any(ix, p.nx), p.nx, 1, ixo);
+    const bool has_halo = tid < 2 * R;
+    const int hex = (tid < R) ? tid : TX + tid;
+    int hxo[2 * RE + 1];
+    axis_offsets<RE>(wrap_any(x0 - R + hex, p.nx), p.nx, 1, hxo);
+    const int zero[2 * RE + 1] = {};
+
+    auto psi_slab = [&](int m) {
+        int mo[2 * RE + 1];
+        axis_offsets<RE>(wrap_near(m, nm), nm, p.nx, mo);
+        Real* dst = ring + ring_slot(m, NS) * E;
+        Real f[Q];
+        gather_off<kLatD2Q9, Real, RE>(P, ixo, mo, zero, f);
+        Real s = Real(0);
+        sfor<Q>([&](auto bI) { s += f[decltype(bI)::value]; });
+        dst[tid + R] = psi_of<kLatD2Q9>(std::is_same<Real, float>::value ? Real(p.rho_bar) + s : s, p);
+        Real* st = stash + static_cast<unsigned>(m + 4 * NST) % NST * (Q * TX) + tid;
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            st[b * TX] = f[b];
+        });
+        if (has_halo) {
+            Real h[Q];
+            gather_off<kLatD2Q9, Real, RE>(P, hxo, mo, zero, h);
+            Real sh = Real(0);
+            sfor<Q>([&](auto bI) { sh += h[decltype(bI)::value]; });
+            dst[hex] = psi_of<kLatD2Q9>(std::is_same<Real, float>::value ? Real(p.rho_bar) + sh : sh, p);
+        }
+    };
+    for (int m = m0 - R; m < m0 + R; ++m) psi_slab(m);
+    const bool active = ix < p.nx;
+    for (int m = m0; m < m1; ++m) {
+        psi_slab(m + R);
+        __syncthreads();
+        if (active) {
+            Real f[Q];
+            const Real* st = stash + static_cast<unsigned>(m + 4 * NST) % NST * (Q * TX) + tid;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                f[b] = st[b * TX];
+            });
+            Real F[3];
+            force_ring<kLatD2Q9, ORD, Real, EX, E, NS>(ring, m, tid + R, 0, p.G, F);
+            collide<kLatD2Q9, 0>(f, F, p);
+            const int c = m * p.nx + ix;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                P.out[b][c] = f[b];
+            });
+        }
+    }
+    (void)L::Q;
+}
+
+// Persistent step kernel: every CTA walks the work list with stride gridDim.x.
+template <class Real>
+__global__ void __launch_bounds__(kBTX) k_batch_step(const BatchDom* __restrict__ doms, const int4* __restrict__ items,
+                                                    const int* __restrict__ nitems, const Real* __restrict__ pool_in,
+                                                    Real* __restrict__ pool_out)
+{
+    __shared__ Real ring[kBNS * kBEX];
+    __shared__ Real stash[(kBMaxR + 1) * kQ9 * kBTX];
+    const int n = *nitems;
+    for (int it = blockIdx.x; it < n; it += gridDim.x) {
+        const int4 w = items[it];
+        const BatchDom d = doms[w.x];
+        const DevParams p = dom_params(d);
+        const Real* A = pool_in + d.off;
+        Real* Bo = pool_out + d.off;
+        const int x0 = w.y * kBTX, m0 = w.z * kBZC;
+        switch (d.order) {
+        case 4: batch_item<4, Real>(A, Bo, p, x0, m0, ring, stash); break;
+        case 6: batch_item<6, Real>(A, Bo, p, x0, m0, ring, stash); break;
+        case 8: batch_item<8, Real>(A, Bo, p, x0, m0, ring, stash); break;
+        default: batch_item<10, Real>(A, Bo, p, x0, m0, ring, stash); break;
+        }
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
+// Per-cell macroscopic values of domain d at cell i (pulled populations, psi of
+// the neighbourhood recomputed from the populations; used by the observables).
+template <int ORD, class Real>
+__device__ void batch_cell_obs(const Real* __restrict__ A, const DevParams& p, int x, int y, double& rho,
+                               double (&mom)[3])
+{
+    using L = Lattice<kLatD2Q9>;
+    using S = Stencil<2, ORD>;
+    auto rho_at = [&](int xx, int yy) {
+        Real f[kQ9];
+        gather<kLatD2Q9>(A, p, wrap_any(xx, p.nx), wrap_any(yy, p.ny), 0, f);
+        Real s = Real(0);
+        sfor<kQ9>([&](auto bI) { s += f[decltype(bI)::value]; });
+        return std::is_same<Real, float>::value ? Real(p.rho_bar) + s : s;
+    };
+    Real f[kQ9];
+    gather<kLatD2Q9>(A, p, x, y, 0, f);
+    double s = 0.0, j[2] = {0.0, 0.0};
+    sfor<kQ9>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1];
+        s += static_cast<double>(f[b]);
+        j[0] += static_cast<double>(f[b]) * cx;
+        j[1] += static_cast<double>(f[b]) * cy;
+    });
+    rho = std::is_same<Real, float>::value ? p.rho_bar + s : s;
+    double acc[2] = {0.0, 0.0};
+    sfor<S::n>([&](auto aI) {
+        constexpr int a = decltype(aI)::value;
+        constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1];
+        constexpr double wt = S::T.w[a] * L::cs2;
+        const double ps = static_cast<double>(psi_of<kLatD2Q9>(rho_at(x + ex, y + ey), p));
+        acc[0] += wt * ps * ex;
+        acc[1] += wt * ps * ey;
+    });
+    const double gp = -p.G * static_cast<double>(psi_of<kLatD2Q9>(static_cast<Real>(rho), p));
+    mom[0] = j[0] + 0.5 * (gp * acc[0]);
+    mom[1] = j[1] + 0.5 * (gp * acc[1]);
+    mom[2] = 0.0;
+}
+
+// Per-domain observables: one block per (domain, block slice); block partials
+// are written per slice and summed per domain in a fixed order by k_batch_obs_final.
+constexpr int kObsSlices = 8;
+template <class Real>
+__global__ void __launch_bounds__(256) k_batch_obs(const BatchDom* __restrict__ doms, const Real* __restrict__ pool,
+                                                   const int* __restrict__ cur_of, const long long pool_stride,
+                                                   double* __restrict__ partials, int ndom)
+{
+    const int d = blockIdx.x / kObsSlices, slice = blockIdx.x % kObsSlices;
+    if (d >= ndom) return;
+    const BatchDom dm = doms[d];
+    const DevParams p = dom_params(dm);
+    const Real* A = pool + dm.off + (cur_of[d] ? pool_stride : 0);
+    double v[kObsWidth] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    bool bad = false;
+    for (long long i = static_cast<long long>(slice) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(kObsSlices) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx), y = static_cast<int>(i / p.nx);
+        double rho, mom[3];
+        switch (dm.order) {
+        case 4: batch_cell_obs<4, Real>(A, p, x, y, rho, mom); break;
+        case 6: batch_cell_obs<6, Real>(A, p, x, y, rho, mom); break;
+        case 8: batch_cell_obs<8, Real>(A, p, x, y, rho, mom); break;
+        default: batch_cell_obs<10, Real>(A, p, x, y, rho, mom); break;
+        }
+        const double ux = mom[0] / rho, uy = mom[1] / rho, uz = 0.0;
+        const double um = sqrt(ux * ux + uy * uy + uz * uz);
+        if (!isfinite(rho) || !isfinite(um)) bad = true;
+        v[0] += rho;
+        v[1] += mom[0];
+        v[2] += mom[1];
+        v[4] += um;
+        v[5] = fmax(v[5], um);
+    }
+    if (bad) v[5] = INFINITY;  // a diverged domain reports max|u| = inf (fmax would skip NaN)
+    block_reduce_obs(v, partials + static_cast<long long>(blockIdx.x) * kObsWidth);
+}
+
+// res[d*8 + 0..5] = sums (max) over the slices; 6: rho at the centre, 7: rho at node 0.
+template <class Real>
+__global__ void k_batch_obs_final(const BatchDom* __restrict__ doms, const Real* __restrict__ pool,
+                                  const int* __restrict__ cur_of, const long long pool_stride,
+                                  const double* __restrict__ partials, double* __restrict__ res, int ndom)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= ndom) return;
+    double acc[kObsWidth];
+    for (int k = 0; k < kObsWidth; ++k) acc[k] = partials[static_cast<long long>(d) * kObsSlices * kObsWidth + k];
+    for (int s = 1; s < kObsSlices; ++s)
+        for (int k = 0; k < kObsWidth; ++k) {
+            const double v = partials[(static_cast<long long>(d) * kObsSlices + s) * kObsWidth + k];
+            acc[k] = (k == kObsWidth - 1) ? fmax(acc[k], v) : acc[k] + v;
+        }
+    for (int k = 0; k < kObsWidth; ++k) res[d * 8 + k] = acc[k];
+    const BatchDom dm = doms[d];
+    const DevParams p = dom_params(dm);
+    const Real* A = pool + dm.off + (cur_of[d] ? pool_stride : 0);
+    auto rho_at = [&](int x, int y) {
+        Real f[kQ9];
+        gather<kLatD2Q9>(A, p, x, y, 0, f);
+        double s = 0.0;
+        for (int b = 0; b < kQ9; ++b) s += static_cast<double>(f[b]);
+        return std::is_same<Real, float>::value ? p.rho_bar + s : s;
+    };
+    res[d * 8 + 6] = rho_at(p.nx / 2, p.ny / 2);
+    res[d * 8 + 7] = rho_at(0, 0);
+}
+
+template <class Real>
+__global__ void k_batch_init(const BatchDom* __restrict__ doms, const double* __restrict__ init, int ndom,
+                             Real* __restrict__ pool)
+{
+    using L = Lattice<kLatD2Q9>;
+    const int d = blockIdx.y;
+    if (d >= ndom) return;
+    const BatchDom dm = doms[d];
+    const DevParams p = dom_params(dm);
+    const double rl = init[4 * d], rg = init[4 * d + 1], R = init[4 * d + 2], W = init[4 * d + 3];
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx), y = static_cast<int>(i / p.nx);
+        sfor<kQ9>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1];
+            constexpr double wb = L::T.w[b];
+            // A_b(y) = w_b rho0(y + c_b): the pulled state is feq(rho0, 0)
+            const int xs = shift_wrap_fwd<cx>(x, p.nx), ys = shift_wrap_fwd<cy>(y, p.ny);
+            const double dx = min_image(xs, p.nx), dy = min_image(ys, p.ny);
+            const double r = sqrt(dx * dx + dy * dy);
+            const double rho0 = 0.5 * (rl + rg) - 0.5 * (rl - rg) * tanh(2.0 * (r - R) / W);
+            const double v = std::is_same<Real, float>::value ? wb * (rho0 - p.rho_bar) : wb * rho0;
+            pool[dm.off + static_cast<long long>(b) * p.N + i] = static_cast<Real>(v);
+        });
+    }
+}
+
+__global__ void k_batch_prev_init(const BatchDom* __restrict__ doms, const double* __restrict__ res,
+                                  double* __restrict__ prev, int ndom)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < ndom && doms[d].active) prev[d] = res[d * 8 + 5];
+}
+
+// Steady check after a block of K steps: retire domain d when
+// |max|u|(t) - max|u|(t-K)| / K < max(tol, floor * max|u| / K).
+__global__ void k_batch_check(BatchDom* __restrict__ doms, const double* __restrict__ res, double* __restrict__ prev,
+                              int ndom, double tol, double floor_rel, int K, int* __restrict__ newly)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= ndom) return;
+    if (!doms[d].active) return;
+    const double u = res[d * 8 + 5];
+    if (!isfinite(u)) {  // diverged: retire it, its observables stay non-finite
+        doms[d].active = 0;
+        atomicAdd(newly, 1);
+        return;
+    }
+    const double thr = fmax(tol, floor_rel * u / K);
+    if (prev[d] >= 0.0 && fabs(u - prev[d]) / K < thr) {
+        doms[d].active = 0;
+        atomicAdd(newly, 1);
+    }
+    prev[d] = u;
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_batch {
+    int n;
+    int fp32;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    lbm_params p0;
+    std::vector<BatchDom> doms;
+    std::vector<double> init;
+    std::vector<int> cur_of;     // buffer holding each domain's state (0: pool A)
+    std::vector<int64_t> steps;  // steps each domain has taken
+    std::vector<int> retired_at_check;
+    long long pool_elems;
+    void* pool[2];
+    BatchDom* d_doms;
+    int4* d_items;
+    int* d_nitems;
+    int* d_cur_of;
+    double* d_init;
+    double* d_partials;
+    double* d_res;
+    double* d_prev;
+    int* d_newly;
+    int* h_newly;  // pinned
+    int nitems;
+    int grid;
+    int cur;  // global parity: pool[cur] holds the state of active domains
+    int64_t global_step;
+    cudaGraphExec_t graph[2];
+    int graph_k;
+    int graph_cur;  // parity the graph was captured from
+
+    void* dalloc(size_t bytes)
+    {
+        if (p0.dev_alloc) return p0.dev_alloc(bytes, p0.alloc_ctx);
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void dfree(void* p)
+    {
+        if (!p) return;
+        if (p0.dev_free)
+            p0.dev_free(p, p0.alloc_ctx);
+        else
+            cudaFree(p);
+    }
+};
+
+namespace {
+
+#define LBM_BCK(call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            char m_[256];                                                                              \
+            std::snprintf(m_, sizeof(m_), "%s: %s", #call, cudaGetErrorString(e_));                    \
+            return set_last_error(LBM_ECUDA, m_);                                                      \
+        }                                                                                              \
+    } while (0)
+
+int rebuild_items(lbm_batch* b)
+{
+    std::vector<int4> items;
+    for (int d = 0; d < b->n; ++d) {
+        if (!b->doms[d].active) continue;
+        for (int c = 0; c < b->doms[d].nch; ++c)
+            for (int t = 0; t < b->doms[d].ntx; ++t) items.push_back(make_int4(d, t, c, 0));
+    }
+    b->nitems = static_cast<int>(items.size());
+    if (!items.empty())
+        LBM_BCK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                                b->stream));
+    LBM_BCK(cudaMemcpyAsync(b->d_nitems, &b->nitems, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    LBM_BCK(cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+cudaError_t launch_step(lbm_batch* b, int parity)
+{
+    if (b->fp32)
+        k_batch_step<float><<<b->grid, kBTX, 0, b->stream>>>(
+            b->d_doms, b->d_items, b->d_nitems, static_cast<const float*>(b->pool[parity]),
+            static_cast<float*>(b->pool[parity ^ 1]));
+    else
+        k_batch_step<double><<<b->grid, kBTX, 0, b->stream>>>(
+            b->d_doms, b->d_items, b->d_nitems, static_cast<const double*>(b->pool[parity]),
+            static_cast<double*>(b->pool[parity ^ 1]));
+    return cudaGetLastError();
+}
+
+// Observables of every domain into d_res (the state pointed to by d_cur_of).
+cudaError_t launch_obs(lbm_batch* b)
+{
+    const long long stride = static_cast<const char*>(b->pool[1]) - static_cast<const char*>(b->pool[0]);
+    const long long es = b->fp32 ? 4 : 8;
+    if (b->fp32) {
+        k_batch_obs<float><<<b->n * kObsSlices, 256, 0, b->stream>>>(
+            b->d_doms, static_cast<const float*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials, b->n);
+        k_batch_obs_final<float><<<(b->n + 63) / 64, 64, 0, b->stream>>>(
+            b->d_doms, static_cast<const float*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials, b->d_res,
+            b->n);
+    } else {
+        k_batch_obs<double><<<b->n * kObsSlices, 256, 0, b->stream>>>(
+            b->d_doms, static_cast<const double*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials, b->n);
+        k_batch_obs_final<double><<<(b->n + 63) / 64, 64, 0, b->stream>>>(
+            b->d_doms, static_cast<const double*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials,
+            b->d_res, b->n);
+    }
+    return cudaGetLastError();
+}
+
+double pressure_exp(double rho, double G)
+{
+    const double ps = -std::expm1(-rho);
+    return rho / 3.0 + 0.5 * G / 3.0 * ps * ps;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch** out)
+{
+    if (!ps || !init || !out || n < 1) return set_last_error(LBM_EINVAL, "lbm_batch_create: bad argument");
+    const int fp32 = ps[0].precision == LBM_FP32_SHIFTED;
+    for (int d = 0; d < n; ++d) {
+        const lbm_params& p = ps[d];
+        const int order = p.stencil == LBM_STENCIL_LATTICE ? 4 : p.stencil;
+        if (p.lattice != LBM_D2Q9 || p.psi != LBM_PSI_EXP || p.collision != LBM_BGK)
+            return set_last_error(LBM_EUNSUPPORTED, "lbm_batch_create: batches are D2Q9, exp psi, BGK");
+        if ((p.precision == LBM_FP32_SHIFTED) != (fp32 != 0))
+            return set_last_error(LBM_EINVAL, "lbm_batch_create: one precision per batch");
+        if (p.nx < 8 || p.ny < 8 || p.nz != 1 || !(p.tau > 0.5) ||
+            !(order == 4 || order == 6 || order == 8 || order == 10))
+            return set_last_error(LBM_EINVAL, "lbm_batch_create: bad domain parameters");
+        if (!(init[4 * d + 3] > 0.0) || !(init[4 * d] > 0.0) || !(init[4 * d + 1] > 0.0))
+            return set_last_error(LBM_EINVAL, "lbm_batch_create: bad initial droplet");
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return set_last_error(LBM_ENOMEM, "host allocation failed");
+    b->n = n;
+    b->fp32 = fp32;
+    b->p0 = ps[0];
+    b->init.assign(init, init + 4 * n);
+    b->cur_of.assign(n, 0);
+    b->steps.assign(n, 0);
+    cudaGetDevice(&b->device);
+    if (ps[0].stream) {
+        b->stream = static_cast<cudaStream_t>(ps[0].stream);
+    } else {
+        cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = true;
+    }
+    long long off = 0;
+    b->doms.resize(n);
+    for (int d = 0; d < n; ++d) {
+        const lbm_params& p = ps[d];
+        BatchDom& m = b->doms[d];
+        m.nx = p.nx;
+        m.ny = p.ny;
+        m.order = p.stencil == LBM_STENCIL_LATTICE ? 4 : p.stencil;
+        m.ntx = (p.nx + kBTX - 1) / kBTX;
+        m.nch = (p.ny + kBZC - 1) / kBZC;
+        m.active = 1;
+        m.off = off;
+        m.G = p.G;
+        m.omega = 1.0 / p.tau;
+        m.pref = 1.0 - 1.0 / (2.0 * p.tau);
+        // FP32 deviations from the mean initial density (rectangle-rule mean of the
+        // tanh droplet, computed on the host in double)
+        double sum = 0.0;
+        if (fp32) {
+            for (int y = 0; y < p.ny; ++y)
+                for (int x = 0; x < p.nx; ++x) {
+                    auto mi = [](int i, int nn) {
+                        double v = (double)i - (double)(nn / 2);
+                        if (v > 0.5 * nn) v -= nn;
+                        if (v < -0.5 * nn) v += nn;
+                        return v;
+                    };
+                    const double dx = mi(x, p.nx), dy = mi(y, p.ny);
+                    const double r = std::sqrt(dx * dx + dy * dy);
+                    sum += 0.5 * (init[4 * d] + init[4 * d + 1]) -
+                           0.5 * (init[4 * d] - init[4 * d + 1]) * std::tanh(2.0 * (r - init[4 * d + 2]) / init[4 * d + 3]);
+                }
+            m.rho_bar = sum / ((double)p.nx * p.ny);
+        }
+        off += (long long)kQ9 * p.nx * p.ny;
+        off = (off + 63) / 64 * 64;  // 256-byte aligned domains
+    }
+    b->pool_elems = off;
+    const size_t es = fp32 ? 4 : 8;
+    long long items = 0;
+    for (auto& m : b->doms) items += (long long)m.ntx * m.nch;
+    b->pool[0] = b->dalloc(es * off);
+    b->pool[1] = b->dalloc(es * off);
+    b->d_doms = static_cast<BatchDom*>(b->dalloc(sizeof(BatchDom) * n));
+    b->d_items = static_cast<int4*>(b->dalloc(sizeof(int4) * items));
+    b->d_nitems = static_cast<int*>(b->dalloc(256));
+    b->d_cur_of = static_cast<int*>(b->dalloc(sizeof(int) * n));
+    b->d_init = static_cast<double*>(b->dalloc(sizeof(double) * 4 * n));
+    b->d_partials = static_cast<double*>(b->dalloc(sizeof(double) * n * kObsSlices * kObsWidth));
+    b->d_res = static_cast<double*>(b->dalloc(sizeof(double) * n * 8));
+    b->d_prev = static_cast<double*>(b->dalloc(sizeof(double) * n));
+    b->d_newly = static_cast<int*>(b->dalloc(256));
+    if (!b->pool[0] || !b->pool[1] || !b->d_doms || !b->d_items || !b->d_nitems || !b->d_cur_of || !b->d_init ||
+        !b->d_partials || !b->d_res || !b->d_prev || !b->d_newly) {
+        lbm_batch_destroy(b);
+        return set_last_error(LBM_ENOMEM, "lbm_batch_create: device allocation failed");
+    }
+    if (cudaMallocHost(&b->h_newly, sizeof(int)) != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return set_last_error(LBM_ENOMEM, "pinned host allocation failed");
+    }
+    int rc = LBM_OK;
+    auto ck = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == LBM_OK) rc = set_last_error(LBM_ECUDA, cudaGetErrorString(e));
+    };
+    ck(cudaMemcpyAsync(b->d_doms, b->doms.data(), sizeof(BatchDom) * n, cudaMemcpyHostToDevice, b->stream));
+    ck(cudaMemcpyAsync(b->d_init, init, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, b->stream));
+    ck(cudaMemsetAsync(b->d_cur_of, 0, sizeof(int) * n, b->stream));
+    std::vector<double> prev(n, -1.0);
+    ck(cudaMemcpyAsync(b->d_prev, prev.data(), sizeof(double) * n, cudaMemcpyHostToDevice, b->stream));
+    ck(cudaMemsetAsync(b->pool[1], 0, es * off, b->stream));
+    int maxp = 1;
+    for (auto& m : b->doms) maxp = std::max(maxp, m.nx * m.ny);
+    const dim3 g((maxp + 255) / 256 < 1024 ? (maxp + 255) / 256 : 1024, n);
+    if (fp32)
+        k_batch_init<float><<<g, 256, 0, b->stream>>>(b->d_doms, b->d_init, n, static_cast<float*>(b->pool[0]));
+    else
+        k_batch_init<double><<<g, 256, 0, b->stream>>>(b->d_doms, b->d_init, n, static_cast<double*>(b->pool[0]));
+    ck(cudaGetLastError());
+    int nsm = 0, occ = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    if (fp32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_step<float>, kBTX, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_step<double>, kBTX, 0);
+    b->grid = std::max(1, nsm * std::max(1, occ));
+    if (rc == LBM_OK) rc = rebuild_items(b);
+    if (rc != LBM_OK) {
+        lbm_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch* b)
+{
+    if (!b) return LBM_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+    b->dfree(b->pool[0]);
+    b->dfree(b->pool[1]);
+    b->dfree(b->d_doms);
+    b->dfree(b->d_items);
+    b->dfree(b->d_nitems);
+    b->dfree(b->d_cur_of);
+    b->dfree(b->d_init);
+    b->dfree(b->d_partials);
+    b->dfree(b->d_res);
+    b->dfree(b->d_prev);
+    b->dfree(b->d_newly);
+    if (b->h_newly) cudaFreeHost(b->h_newly);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return LBM_OK;
+}
+
+// Advances every active domain by n steps (no steady check).
+int lbm_batch_step(lbm_batch* b, int64_t n)
+{
+    if (!b || n < 0) return set_last_error(LBM_EINVAL, "lbm_batch_step: bad argument");
+    LBM_BCK(cudaSetDevice(b->device));
+    for (int64_t i = 0; i < n; ++i) {
+        LBM_BCK(launch_step(b, b->cur));
+        b->cur ^= 1;
+    }
+    b->global_step += n;
+    for (int d = 0; d < b->n; ++d)
+        if (b->doms[d].active) {
+            b->steps[d] += n;
+            b->cur_of[d] = b->cur;
+        }
+    LBM_BCK(cudaMemcpyAsync(b->d_cur_of, b->cur_of.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, b->stream));
+    return LBM_OK;
+}
+
+int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t check_every,
+                            int64_t* steps_per_domain, lbm_obs* obs_per_domain)
+{
+    if (!b || !(tol > 0.0) || max_steps < 0 || check_every < 2 || check_every % 2)
+        return set_last_error(LBM_EINVAL, "lbm_batch_run_to_steady: bad argument (check_every must be even)");
+    LBM_BCK(cudaSetDevice(b->device));
+    const int K = static_cast<int>(check_every);
+    const double floor_rel = b->fp32 ? 1e-6 : 0.0;
+    // one graph per starting parity is not needed: K is even, so every block of K
+    // steps starts from the same parity
+    if (!b->graph[0] || b->graph_k != K || b->graph_cur != b->cur) {
+        if (b->graph[0]) cudaGraphExecDestroy(b->graph[0]);
+        b->graph[0] = nullptr;
+        cudaGraph_t g = nullptr;
+        LBM_BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < K && e == cudaSuccess; ++i) e = launch_step(b, (b->cur + i) & 1);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_newly, 0, sizeof(int), b->stream);
+        if (e == cudaSuccess) e = launch_obs(b);
+        if (e == cudaSuccess) {
+            k_batch_check<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_doms, b->d_res, b->d_prev, b->n, tol,
+                                                                    floor_rel, K, b->d_newly);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_newly, b->d_newly, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return set_last_error(LBM_ECUDA, cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&b->graph[0], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return set_last_error(LBM_ECUDA, cudaGetErrorString(e));
+        b->graph_k = K;
+        b->graph_cur = b->cur;
+    }
+    // the observables inside the graph read cur_of: active domains end each block
+    // on the same parity as they started (K even)
+    for (int d = 0; d < b->n; ++d)
+        if (b->doms[d].active) b->cur_of[d] = b->cur;
+    LBM_BCK(cudaMemcpyAsync(b->d_cur_of, b->cur_of.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, b->stream));
+    // the first check compares against max|u| of the state the run starts from
+    LBM_BCK(launch_obs(b));
+    k_batch_prev_init<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_doms, b->d_res, b->d_prev, b->n);
+    LBM_BCK(cudaGetLastError());
+    int64_t taken = 0;
+    int nactive = 0;
+    for (auto& m : b->doms) nactive += m.active;
+    while (nactive > 0 && taken + K <= max_steps) {
+        LBM_BCK(cudaGraphLaunch(b->graph[0], b->stream));
+        LBM_BCK(cudaStreamSynchronize(b->stream));
+        taken += K;
+        b->global_step += K;
+        for (int d = 0; d < b->n; ++d)
+            if (b->doms[d].active) b->steps[d] += K;
+        if (*b->h_newly > 0) {
+            std::vector<BatchDom> dv(b->n);
+            LBM_BCK(cudaMemcpy(dv.data(), b->d_doms, sizeof(BatchDom) * b->n, cudaMemcpyDeviceToHost));
+            for (int d = 0; d < b->n; ++d) b->doms[d].active = dv[d].active;
+            nactive = 0;
+            for (auto& m : b->doms) nactive += m.active;
+            if (int rc = rebuild_items(b)) return rc;
+        }
+    }
+    LBM_BCK(launch_obs(b));
+    std::vector<double> res(8 * (size_t)b->n);
+    LBM_BCK(cudaMemcpyAsync(res.data(), b->d_res, sizeof(double) * 8 * b->n, cudaMemcpyDeviceToHost, b->stream));
+    LBM_BCK(cudaStreamSynchronize(b->stream));
+    for (int d = 0; d < b->n; ++d) {
+        if (steps_per_domain) steps_per_domain[d] = b->steps[d];
+        if (obs_per_domain) {
+            lbm_obs o{};
+            const double* r = &res[8 * (size_t)d];
+            const double N = (double)b->doms[d].nx * b->doms[d].ny;
+            o.mass = r[0];
+            o.mom[0] = r[1];
+            o.mom[1] = r[2];
+            o.mean_u = r[4] / N;
+            o.max_u = r[5];
+            o.rho_l = r[6];
+            o.rho_g = r[7];
+            o.dp = pressure_exp(o.rho_l, b->doms[d].G) - pressure_exp(o.rho_g, b->doms[d].G);
+            o.step = b->steps[d];
+            obs_per_domain[d] = o;
+        }
+    }
+    return nactive == 0 ? LBM_OK : set_last_error(LBM_ENOTCONVERGED, "some domains still changing at max_steps");
+}
+
+// Observables of every domain in its current state.
+int lbm_batch_observables(lbm_batch* b, lbm_obs* obs_per_domain)
+{
+    if (!b || !obs_per_domain) return set_last_error(LBM_EINVAL, "lbm_batch_observables: bad argument");
+    LBM_BCK(cudaSetDevice(b->device));
+    LBM_BCK(cudaMemcpyAsync(b->d_cur_of, b->cur_of.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, b->stream));
+    LBM_BCK(launch_obs(b));
+    std::vector<double> res(8 * (size_t)b->n);
+    LBM_BCK(cudaMemcpyAsync(res.data(), b->d_res, sizeof(double) * 8 * b->n, cudaMemcpyDeviceToHost, b->stream));
+    LBM_BCK(cudaStreamSynchronize(b->stream));
+    for (int d = 0; d < b->n; ++d) {
+        lbm_obs o{};
+        const double* r = &res[8 * (size_t)d];
+        const double N = (double)b->doms[d].nx * b->doms[d].ny;
+        o.mass = r[0];
+        o.mom[0] = r[1];
+        o.mom[1] = r[2];
+        o.mean_u = r[4] / N;
+        o.max_u = r[5];
+        o.rho_l = r[6];
+        o.rho_g = r[7];
+        o.dp = pressure_exp(o.rho_l, b->doms[d].G) - pressure_exp(o.rho_g, b->doms[d].G);
+        o.step = b->steps[d];
+        obs_per_domain[d] = o;
+    }
+    return LBM_OK;
+}
+
+// Sets domain d's pre-collision populations from a double host array [9][ny][nx]
+// (in the pool buffer that holds its state).
+int lbm_batch_set_populations(lbm_batch* b, int d, const double* f_host)
+{
+    if (!b || !f_host || d < 0 || d >= b->n) return set_last_error(LBM_EINVAL, "lbm_batch_set_populations: bad argument");
+    LBM_BCK(cudaSetDevice(b->device));
+    const BatchDom& m = b->doms[d];
+    const long long N = (long long)m.nx * m.ny;
+    const size_t es = b->fp32 ? 4 : 8;
+    std::vector<unsigned char> raw(es * kQ9 * N);
+    static const int cx[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+    static const int cy[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+    static const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    // stream on the host: A_b(y) = f_b(y + c_b)
+    for (int q = 0; q < kQ9; ++q)
+        for (int y = 0; y < m.ny; ++y)
+            for (int x = 0; x < m.nx; ++x) {
+                const int xs = (x + cx[q] + m.nx) % m.nx, ys = (y + cy[q] + m.ny) % m.ny;
+                const double v = f_host[(long long)q * N + (long long)ys * m.nx + xs];
+                const long long i = (long long)q * N + (long long)y * m.nx + x;
+                if (b->fp32) {
+                    const float fv = static_cast<float>(v - w[q] * m.rho_bar);
+                    std::memcpy(&raw[4 * i], &fv, 4);
+                } else {
+                    std::memcpy(&raw[8 * i], &v, 8);
+                }
+            }
+    char* dst = static_cast<char*>(b->pool[b->cur_of[d]]) + es * m.off;
+    LBM_BCK(cudaMemcpyAsync(dst, raw.data(), raw.size(), cudaMemcpyHostToDevice, b->stream));
+    LBM_BCK(cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+// Pre-collision populations of domain d in double, [9][ny][nx].
+int lbm_batch_get_populations(lbm_batch* b, int d, double* f_host)
+{
+    if (!b || !f_host || d < 0 || d >= b->n) return set_last_error(LBM_EINVAL, "lbm_batch_get_populations: bad argument");
+    LBM_BCK(cudaSetDevice(b->device));
+    const BatchDom& m = b->doms[d];
+    const long long N = (long long)m.nx * m.ny;
+    const size_t es = b->fp32 ? 4 : 8;
+    std::vector<unsigned char> raw(es * kQ9 * N);
+    const char* src = static_cast<const char*>(b->pool[b->cur_of[d]]) + es * m.off;
+    LBM_BCK(cudaMemcpyAsync(raw.data(), src, raw.size(), cudaMemcpyDeviceToHost, b->stream));
+    LBM_BCK(cudaStreamSynchronize(b->stream));
+    // un-stream on the host: f_b(x) = A_b(x - c_b)
+    static const int cx[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+    static const int cy[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+    static const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    for (int q = 0; q < kQ9; ++q)
+        for (int y = 0; y < m.ny; ++y)
+            for (int x = 0; x < m.nx; ++x) {
+                const int xs = ((x - cx[q]) % m.nx + m.nx) % m.nx, ys = ((y - cy[q]) % m.ny + m.ny) % m.ny;
+                const long long i = (long long)q * N + (long long)ys * m.nx + xs;
+                double v;
+                if (b->fp32) {
+                    float fv;
+                    std::memcpy(&fv, &raw[4 * i], 4);
+                    v = (double)fv + w[q] * m.rho_bar;
+                } else {
+                    std::memcpy(&v, &raw[8 * i], 8);
+                }
+                f_host[(long long)q * N + (long long)y * m.nx + x] = v;
+            }
+    return LBM_OK;
+}
+
+}  // extern "C"

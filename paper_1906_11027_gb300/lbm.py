@@ -95,6 +95,13 @@ _SIGNATURES = {
     "lbm_load": (_I, [_P, ctypes.c_char_p]),
     "lbm_bytes_per_update": (_D, [_P]),
     "lbm_moments_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _dp]),
+    "lbm_batch_create": (_I, [ctypes.POINTER(lbm_params), _dp, _I, ctypes.POINTER(_P)]),
+    "lbm_batch_destroy": (_I, [_P]),
+    "lbm_batch_step": (_I, [_P, _L]),
+    "lbm_batch_run_to_steady": (_I, [_P, _D, _L, _L, ctypes.POINTER(_L), ctypes.POINTER(lbm_obs)]),
+    "lbm_batch_observables": (_I, [_P, ctypes.POINTER(lbm_obs)]),
+    "lbm_batch_get_populations": (_I, [_P, _I, _dp]),
+    "lbm_batch_set_populations": (_I, [_P, _I, _dp]),
     "lbm_strerror": (ctypes.c_char_p, [_I]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -253,6 +260,103 @@ def lbm_moments_noalloc(f_dev, lattice, precision, nx, ny, nz, rho_bar=0.0, stre
     _check(load().lbm_moments_noalloc(f_dev, lattice, precision, nx, ny, nz, rho_bar, stream,
                                       _dptr(out)), "lbm_moments_noalloc")
     return out
+
+
+def lbm_batch_create(params_list, init) -> int:
+    n = len(params_list)
+    arr = (lbm_params * n)(*params_list)
+    init = np.ascontiguousarray(init, dtype=np.float64).reshape(-1)
+    assert init.size == 4 * n
+    h = _P()
+    _check(load().lbm_batch_create(arr, _dptr(init), n, ctypes.byref(h)), "lbm_batch_create")
+    return h.value
+
+
+def lbm_batch_destroy(b) -> None:
+    _check(load().lbm_batch_destroy(b), "lbm_batch_destroy")
+
+
+def lbm_batch_step(b, n: int) -> None:
+    _check(load().lbm_batch_step(b, int(n)), "lbm_batch_step")
+
+
+def lbm_batch_run_to_steady(b, n_domains, tol, max_steps, check_every=100):
+    steps = (_L * n_domains)()
+    obs = (lbm_obs * n_domains)()
+    code = load().lbm_batch_run_to_steady(b, tol, int(max_steps), int(check_every), steps, obs)
+    if code not in (LBM_OK, LBM_ENOTCONVERGED):
+        raise LbmError(code, "lbm_batch_run_to_steady")
+    return list(steps), [o.as_dict() for o in obs], code == LBM_OK
+
+
+def lbm_batch_observables(b, n_domains):
+    obs = (lbm_obs * n_domains)()
+    _check(load().lbm_batch_observables(b, obs), "lbm_batch_observables")
+    return [o.as_dict() for o in obs]
+
+
+def lbm_batch_get_populations(b, d, nx, ny):
+    out = np.empty(9 * nx * ny)
+    _check(load().lbm_batch_get_populations(b, int(d), _dptr(out)), "lbm_batch_get_populations")
+    return out.reshape(9, 1, ny, nx)
+
+
+def lbm_batch_set_populations(b, d, f) -> None:
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+    _check(load().lbm_batch_set_populations(b, int(d), _dptr(f)), "lbm_batch_set_populations")
+
+
+class Batch:
+    """Owner of one lbm_batch: domains = list of dicts with nx, ny, G, tau,
+    stencil, rho_l, rho_g, R, width."""
+
+    def __init__(self, domains, precision=LBM_FP32_SHIFTED, stream=None, torch_alloc=False):
+        self._alloc = None
+        plist = []
+        init = []
+        for d in domains:
+            p = lbm_params_default()
+            p.nx, p.ny, p.nz = d["nx"], d["ny"], 1
+            p.G, p.tau, p.stencil = d["G"], d["tau"], d.get("stencil", 4)
+            p.precision = precision
+            plist.append(p)
+            init += [d["rho_l"], d["rho_g"], d["R"], d["width"]]
+        if stream is not None:
+            plist[0].stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        if torch_alloc:
+            self._alloc = TorchAllocator(stream=stream)
+            plist[0].dev_alloc = self._alloc.alloc_fn
+            plist[0].dev_free = self._alloc.free_fn
+        self.domains = list(domains)
+        self.n = len(domains)
+        self.h = lbm_batch_create(plist, init)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n):
+        lbm_batch_step(self.h, n)
+
+    def run_to_steady(self, tol, max_steps, check_every=100):
+        return lbm_batch_run_to_steady(self.h, self.n, tol, max_steps, check_every)
+
+    def observables(self):
+        return lbm_batch_observables(self.h, self.n)
+
+    def get_f(self, d):
+        dd = self.domains[d]
+        return lbm_batch_get_populations(self.h, d, dd["nx"], dd["ny"])
+
+    def set_f(self, d, f):
+        lbm_batch_set_populations(self.h, d, f)
 
 
 def lbm_strerror(code: int) -> str:
