@@ -396,6 +396,79 @@ def run_sweep(args):
     return 0
 
 
+def run_warmstart(args):
+    """Learned warm start: batched sweep -> steady profiles -> network trained on the
+    GPU (held-out domains for validation) -> plain tanh vs learned start on
+    held-out domains, a D2Q9 512^2 droplet and a D3Q19 128^3 droplet."""
+    import torch
+    from paper_1906_11027_gb300 import inputs, lbm, warmstart
+
+    lbm.load()
+    doms = inputs.sweep_domains(args.sweep_domains)
+    t0 = time.perf_counter()
+    b = lbm.Batch(doms, precision=lbm.LBM_FP32_SHIFTED)
+    steps, obs, _ = b.run_to_steady(1e-10, args.sweep_max_steps, 100)
+    t_sweep = time.perf_counter() - t0
+    Xt, yt, Xv, yv, held = warmstart.dataset_from_batch(b, doms, obs)
+    b.close()
+    t0 = time.perf_counter()
+    net, loss = warmstart.train(Xt, yt, epochs=args.ws_epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    val_mse = float(np.mean((net.predict(Xv) - yv) ** 2)) if len(yv) else None
+
+    def compare(make, init_plain, init_warm, tol, max_steps):
+        out = {}
+        for mode in ("plain", "warm"):
+            dom = make()
+            t1 = time.perf_counter()
+            fb = None
+            if mode == "plain":
+                init_plain(dom)
+            else:
+                fb, _ = init_warm(dom)
+            s, ok = dom.run_to_steady(tol, max_steps, 100)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t1
+            o = dom.observables()
+            out[mode] = dict(steps=s, ok=ok, s=dt, max_u=o["max_u"], rho=dom.fields()["rho"], fallback=fb)
+            dom.close()
+        return {"steps_plain": out["plain"]["steps"], "steps_warm": out["warm"]["steps"],
+                "time_plain_s": round(out["plain"]["s"], 3), "time_warm_s": round(out["warm"]["s"], 3),
+                "converged": [out["plain"]["ok"], out["warm"]["ok"]], "fallback": out["warm"]["fallback"],
+                "max_abs_drho": float(np.abs(out["plain"]["rho"] - out["warm"]["rho"]).max()),
+                "max_u_rel_diff": abs(out["warm"]["max_u"] / out["plain"]["max_u"] - 1.0)}
+
+    heldout = []
+    for i in held[:args.ws_heldout]:
+        d = doms[i]
+        r = compare(lambda d=d: lbm.Domain(d["nx"], d["ny"], G=d["G"], tau=d["tau"], stencil=d["stencil"]),
+                    lambda dom, d=d: dom.init_droplet(d["rho_l"], d["rho_g"], d["R"], d["width"]),
+                    lambda dom, d=d: dom.init_droplet_learned(net, d["R"], d["rho_l"], d["rho_g"], d["width"]),
+                    1e-12, 400000)
+        r.update(L=d["nx"], G=round(d["G"], 3), tau=d["tau"], order=d["stencil"], R=round(d["R"], 1))
+        heldout.append(r)
+    big2 = compare(lambda: lbm.Domain(512, 512, G=-5.0, tau=1.0, stencil=4),
+                   lambda dom: dom.init_droplet(2.0, 0.15, 100.0, 2.0),
+                   lambda dom: dom.init_droplet_learned(net, 100.0, 2.0, 0.15, 2.0), 1e-12, 600000)
+    big3 = compare(lambda: lbm.Domain(128, 128, 128, lattice=lbm.LBM_D3Q19, G=-5.0, tau=1.0,
+                                      precision=lbm.LBM_FP32_SHIFTED),
+                   lambda dom: dom.init_droplet(2.0, 0.15, 30.0, 2.0),
+                   lambda dom: dom.init_droplet_learned(net, 30.0, 2.0, 0.15, 2.0), 1e-10, 200000)
+    used = [h for h in heldout if not h["fallback"]]
+    line = {
+        "metric": "warm_start_steps_saved", "unit": "fraction of plain steps",
+        "value": round(float(np.mean([1 - h["steps_warm"] / h["steps_plain"] for h in used])), 4) if used else None,
+        "higher_is_better": True, "n_gpus": 1, "dtype": "bf16/f32 network, f64 runs", "data": "synthetic",
+        "config": {"workload": "learned_warm_start", "sweep_domains": len(doms), "train_samples": int(len(yt)),
+                   "val_samples": int(len(yv)), "heldout_domains": len(held), "epochs": args.ws_epochs},
+        "sweep_s": round(t_sweep, 2), "train_s": round(t_train, 2), "train_loss": loss, "val_mse": val_mse,
+        "heldout": heldout, "d2q9_512": big2, "d3q19_128_fp32": big3,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,6 +482,9 @@ def main():
     ap.add_argument("--sweep-domains", type=int, default=64)
     ap.add_argument("--sweep-max-steps", type=int, default=200000)
     ap.add_argument("--sweep-details", action="store_true")
+    ap.add_argument("--warmstart", action="store_true", help="train and evaluate the learned warm start")
+    ap.add_argument("--ws-epochs", type=int, default=80)
+    ap.add_argument("--ws-heldout", type=int, default=12)
     ap.add_argument("--fp64-below", type=float, default=1e-6,
                     help="steady max|u| under which an FP32 domain is re-converged in FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -417,6 +493,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.sweep:
         return run_sweep(args)
+    if args.warmstart:
+        return run_warmstart(args)
     world, rank, local = dist_setup(args)
     try:
         if args.impl == "reference":

@@ -241,6 +241,49 @@ int lbm_batch_observables(lbm_batch* b, lbm_obs* obs_per_domain);
 int lbm_batch_get_populations(lbm_batch* b, int d, double* f_host);
 int lbm_batch_set_populations(lbm_batch* b, int d, const double* f_host);
 
+/* ---- learned warm start ------------------------------------------------------ */
+
+/* A multilayer perceptron 5 -> 128 -> 128 -> 128 -> 128 -> 1 with SiLU activations
+ * that maps scaled features (G, tau, stencil order, R, signed distance d to the
+ * interface) to the steady density of a droplet, trained on steady profiles the
+ * method itself produces; it only initialises the relaxation (the LB step decides
+ * the result).  Weights are FP32 masters with BF16 copies; the GEMMs of training
+ * and inference run on the tensor cores with FP32 accumulation.
+ * Features (lbm_mlp_features): ((G + 4.9)/0.6, (tau - 0.8)/0.2, (order - 7)/3,
+ * (R - 40)/30, d/12).  Parameter vector: W1 [5][128], b1, W2 [128][128], b2, W3,
+ * b3, W4, b4, W5 [128][1], b5 (50,433 floats); z = h W + b. */
+typedef struct lbm_mlp lbm_mlp;
+int lbm_mlp_create(lbm_mlp** out, uint64_t seed);   /* He-uniform weights from SplitMix64(seed) */
+int lbm_mlp_destroy(lbm_mlp* net);
+int lbm_mlp_num_params(void);
+int lbm_mlp_get_params(const lbm_mlp* net, float* params_out);
+int lbm_mlp_set_params(lbm_mlp* net, const float* params);
+/* raw: n x (G, tau, order, R, d) doubles -> out: n x 5 scaled floats */
+int lbm_mlp_features(const double* raw, int64_t n, float* out);
+/* y[i] = network(X[i]) for n scaled feature rows (host arrays) */
+int lbm_mlp_predict(lbm_mlp* net, const float* X, int64_t n, float* y);
+/* mean-squared-error loss of one batch and its gradient w.r.t. every parameter */
+int lbm_mlp_loss_grad(lbm_mlp* net, const float* X, const float* y, int n, double* loss, float* grad_out);
+/* Adam (lr, beta 0.9/0.999, eps 1e-8) over `epochs` passes of mini-batches of
+ * `batch` rows (a SplitMix64 permutation per epoch); *final_loss = mean loss of
+ * the last epoch. */
+int lbm_mlp_train(lbm_mlp* net, const float* X, const float* y, int64_t n, int epochs, double lr, int batch,
+                  double* final_loss);
+int lbm_mlp_save(const lbm_mlp* net, const char* path);
+int lbm_mlp_load(lbm_mlp** out, const char* path);
+
+/* Warm start of a centred droplet (psi = 1 - exp(-rho) contexts): the density is
+ * the network's profile for the context's G, tau and stencil order at radius
+ * R_eff, R_eff chosen by bisection so that the total mass equals that of the
+ * tanh droplet (rho_l, rho_g, R, width) of lbm_init_droplet, the remainder removed
+ * by a uniform shift; populations f = w_b rho0.  Falls back to the tanh droplet
+ * (*used_fallback = 1) if the network gives a non-finite or non-positive
+ * density, and for G > -4.5, where close to the critical coupling G_c = -4 the
+ * steady state (droplet or none) depends on the initial state.  *R_eff_out (may
+ * be NULL) = the radius used. */
+int lbm_init_droplet_learned(lbm_ctx* ctx, lbm_mlp* net, double R, double rho_l, double rho_g, double width,
+                             int* used_fallback, double* R_eff_out);
+
 /* Mass and momentum totals of a population buffer, computed without allocating
  * anything.  The paper has no counterpart: this serves callers that cannot
  * allocate device memory at the moment they need the totals, such as an

@@ -105,6 +105,10 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn()
 }
 
 constexpr int kGraphSteps = 16;   // steps per captured graph (even)
+// Couplings weaker than this use the tanh start in lbm_init_droplet_learned:
+// within ~0.5 of G_c = -4 a droplet may dissolve or persist depending on the
+// initial state, so a learned start need not reach the plain run's steady state.
+constexpr double kWarmStartMaxG = -4.5;
 constexpr int kNBlocksMax = 152 * 16;
 constexpr uint32_t kMagic = 0x4c424d31u;  // "LBM1"
 
@@ -594,6 +598,92 @@ int lbm_init_flat(lbm_ctx* c, double rho_l, double rho_g, double width, int axis
     a.a0 = rho_l; a.a1 = rho_g; a.a2 = 0.0; a.a3 = width;
     LBM_CK(c->ks.init_profile(a, c->stream));
     int rc = init_from_device_rho(c, rho0.d());
+    LBM_CK(cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
+// Learned warm start: rho0(r) = network(G, tau, order, R_eff, r - R_eff), R_eff bisected
+// so that the mass equals the tanh droplet's (rho_l, rho_g, R, width), the rest
+// of the mass difference removed by a uniform shift.  Falls back to the tanh
+// profile if the network gives a non-finite or non-positive density.
+int lbm_init_droplet_learned(lbm_ctx* c, lbm_mlp* net, double R, double rho_l, double rho_g, double width,
+                             int* used_fallback, double* R_eff_out)
+{
+    if (!c || !net || !(R > 0.0) || !(width > 0.0) || !(rho_l > 0.0) || !(rho_g > 0.0))
+        return fail(LBM_EINVAL, "bad argument");
+    if (c->prm.psi != LBM_PSI_EXP) return fail(LBM_EUNSUPPORTED, "the warm-start network models psi = 1 - exp(-rho)");
+    if (int rc = set_device(c)) return rc;
+    if (used_fallback) *used_fallback = 0;
+    if (c->prm.G > kWarmStartMaxG) {  // near the critical coupling the steady state depends on the start
+        if (used_fallback) *used_fallback = 1;
+        if (R_eff_out) *R_eff_out = R;
+        return lbm_init_droplet(c, rho_l, rho_g, R, width);
+    }
+    Scratch rho0(c, sizeof(double) * c->N);
+    constexpr int T = 1024;
+    constexpr double kDmax = 12.0;
+    Scratch table(c, sizeof(float) * T);
+    if (!rho0.p || !table.p) return fail(LBM_ENOMEM, "scratch allocation failed");
+    // target mass of the tanh start
+    LaunchArgs a = c->args();
+    a.dbuf0 = rho0.d();
+    a.mode = 0;
+    a.a0 = rho_l; a.a1 = rho_g; a.a2 = R; a.a3 = width;
+    LBM_CK(c->ks.init_profile(a, c->stream));
+    double m0 = 0.0;
+    if (int rc = field_mean(c, rho0.d(), &m0)) return rc;
+    const int dim = c->li.D;
+    auto mass_at = [&](double Re, double* mean) -> int {
+        if (int rc = mlp_profile_table(net, c->prm.G, c->prm.tau, (double)c->order, Re, T, kDmax,
+                                       static_cast<float*>(table.p)))
+            return rc;
+        LBM_CK(launch_field_from_table(c->dp, dim, static_cast<const float*>(table.p), T, kDmax, Re, rho0.d(),
+                                       c->stream));
+        return field_mean(c, rho0.d(), mean);
+    };
+    // the steady radius can differ much from R when the tanh densities are far
+    // from coexistence (small droplet, large box): bracket the whole box
+    int nmin = std::min(c->prm.nx, c->prm.ny);
+    if (dim == 3) nmin = std::min(nmin, c->prm.nz);
+    double lo = 1.0, hi = 0.5 * nmin, mlo = 0.0, mhi = 0.0;
+    int rc = mass_at(lo, &mlo);
+    if (rc == LBM_OK) rc = mass_at(hi, &mhi);
+    if (rc != LBM_OK) return rc;
+    bool ok = std::isfinite(mlo) && std::isfinite(mhi) && (mlo - m0) * (mhi - m0) < 0.0;
+    double Re = R;
+    for (int it = 0; ok && it < 48; ++it) {
+        Re = 0.5 * (lo + hi);
+        double mm = 0.0;
+        if (int r2 = mass_at(Re, &mm)) return r2;
+        if (!std::isfinite(mm)) {
+            ok = false;
+            break;
+        }
+        if ((mm - m0) * (mlo - m0) > 0.0) {
+            lo = Re;
+            mlo = mm;
+        } else {
+            hi = Re;
+        }
+    }
+    if (ok) {
+        double mm = 0.0;
+        if (int r2 = mass_at(Re, &mm)) return r2;
+        LBM_CK(launch_add_constant(rho0.d(), c->N, m0 - mm, c->stream));
+        // the shifted field must stay a valid density
+        std::vector<float> tab(T);
+        LBM_CK(cudaMemcpyAsync(tab.data(), table.p, sizeof(float) * T, cudaMemcpyDeviceToHost, c->stream));
+        LBM_CK(cudaStreamSynchronize(c->stream));
+        for (float v : tab)
+            if (!std::isfinite(v) || v + (m0 - mm) <= 0.0) ok = false;
+    }
+    if (!ok) {  // fallback: the plain tanh droplet
+        if (used_fallback) *used_fallback = 1;
+        LBM_CK(c->ks.init_profile(a, c->stream));
+        Re = R;
+    }
+    if (R_eff_out) *R_eff_out = Re;
+    rc = init_from_device_rho(c, rho0.d());
     LBM_CK(cudaStreamSynchronize(c->stream));
     return rc;
 }

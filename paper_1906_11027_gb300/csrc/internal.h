@@ -89,6 +89,20 @@ cudaError_t launch_sum_partials(const double* partials, int nblocks, int width, 
 cudaError_t launch_mean(const double* x, long long n, double* partials, int nblocks_max,
                         double* res, cudaStream_t s);
 
+// Warm-start network (mlp.cu): evaluates the network's density at T signed
+// distances evenly spaced over [-dmax, dmax] for (G, tau, order, R) into table_dev.
+}  // namespace lbm
+struct lbm_mlp;
+namespace lbm {
+int mlp_profile_table(lbm_mlp* n, double G, double tau, double order, double R, int T, double dmax,
+                      float* table_dev);
+
+// Density field from a radial profile table (reduce.cu): rho0(cell) = table(r - R)
+// with r the periodic distance to the centre node, linear interpolation, clamped.
+cudaError_t launch_field_from_table(const DevParams& p, int dim, const float* table, int T, double dmax, double R,
+                                    double* rho0, cudaStream_t s);
+cudaError_t launch_add_constant(double* x, long long n, double c, cudaStream_t s);
+
 // Per-lattice lookup (defined in kernels_<lattice>.cu). Returns false if the
 // combination is not instantiated.
 bool kernels_d2q9(int order, int coll, int fp32, KernelSet* ks);

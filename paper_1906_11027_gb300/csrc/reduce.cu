@@ -73,4 +73,55 @@ cudaError_t launch_mean(const double* x, long long n, double* partials, int nblo
     return cudaGetLastError();
 }
 
+__device__ __forceinline__ double centre_offset(int i, int n)
+{
+    double d = static_cast<double>(i) - static_cast<double>(n / 2);
+    if (d > 0.5 * n) d -= n;
+    if (d < -0.5 * n) d += n;
+    return d;
+}
+
+__global__ void k_field_from_table(DevParams p, int dim, const float* __restrict__ table, int T, double dmax,
+                                   double R, double* __restrict__ rho0)
+{
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx);
+        const long long r = i / p.nx;
+        const int y = static_cast<int>(r % p.ny);
+        const int z = static_cast<int>(r / p.ny);
+        const double dx = centre_offset(x, p.nx), dy = centre_offset(y, p.ny);
+        const double dz = dim == 3 ? centre_offset(z, p.nz) : 0.0;
+        double d = sqrt(dx * dx + dy * dy + dz * dz) - R;
+        d = fmin(fmax(d, -dmax), dmax);
+        const double u = (d + dmax) / (2.0 * dmax) * (T - 1);
+        int k = static_cast<int>(floor(u));
+        if (k > T - 2) k = T - 2;
+        const double a = u - k;
+        rho0[i] = (1.0 - a) * static_cast<double>(table[k]) + a * static_cast<double>(table[k + 1]);
+    }
+}
+
+__global__ void k_add_constant(double* __restrict__ x, long long n, double c)
+{
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        x[i] += c;
+}
+
+cudaError_t launch_field_from_table(const DevParams& p, int dim, const float* table, int T, double dmax, double R,
+                                    double* rho0, cudaStream_t s)
+{
+    const long long nb = (p.N + 255) / 256;
+    k_field_from_table<<<static_cast<int>(nb < 2432 ? nb : 2432), 256, 0, s>>>(p, dim, table, T, dmax, R, rho0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_constant(double* x, long long n, double c, cudaStream_t s)
+{
+    const long long nb = (n + 255) / 256;
+    k_add_constant<<<static_cast<int>(nb < 2432 ? nb : 2432), 256, 0, s>>>(x, n, c);
+    return cudaGetLastError();
+}
+
 }  // namespace lbm

@@ -102,6 +102,20 @@ _SIGNATURES = {
     "lbm_batch_observables": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_batch_get_populations": (_I, [_P, _I, _dp]),
     "lbm_batch_set_populations": (_I, [_P, _I, _dp]),
+    "lbm_mlp_create": (_I, [ctypes.POINTER(_P), ctypes.c_uint64]),
+    "lbm_mlp_destroy": (_I, [_P]),
+    "lbm_mlp_num_params": (_I, []),
+    "lbm_mlp_get_params": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "lbm_mlp_set_params": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "lbm_mlp_features": (_I, [_dp, _L, ctypes.POINTER(ctypes.c_float)]),
+    "lbm_mlp_predict": (_I, [_P, ctypes.POINTER(ctypes.c_float), _L, ctypes.POINTER(ctypes.c_float)]),
+    "lbm_mlp_loss_grad": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _I,
+                               ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_float)]),
+    "lbm_mlp_train": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _L, _I, _D, _I,
+                           ctypes.POINTER(_D)]),
+    "lbm_mlp_save": (_I, [_P, ctypes.c_char_p]),
+    "lbm_mlp_load": (_I, [ctypes.POINTER(_P), ctypes.c_char_p]),
+    "lbm_init_droplet_learned": (_I, [_P, _P, _D, _D, _D, _D, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "lbm_strerror": (ctypes.c_char_p, [_I]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -359,6 +373,93 @@ class Batch:
         lbm_batch_set_populations(self.h, d, f)
 
 
+_fptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))  # noqa: E731
+
+
+class MLP:
+    """The warm-start network (lbm_mlp_*): parameters on the GPU, training and
+    inference by the library's kernels."""
+
+    def __init__(self, seed=1906, handle=None):
+        if handle is None:
+            h = _P()
+            _check(load().lbm_mlp_create(ctypes.byref(h), int(seed)), "lbm_mlp_create")
+            handle = h.value
+        self.h = handle
+
+    @classmethod
+    def load_file(cls, path):
+        h = _P()
+        _check(load().lbm_mlp_load(ctypes.byref(h), path.encode()), "lbm_mlp_load")
+        return cls(handle=h.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def num_params():
+        return load().lbm_mlp_num_params()
+
+    @staticmethod
+    def features(raw):
+        raw = np.ascontiguousarray(raw, dtype=np.float64).reshape(-1, 5)
+        out = np.empty(raw.shape, dtype=np.float32)
+        _check(load().lbm_mlp_features(_dptr(raw), len(raw), _fptr(out)), "lbm_mlp_features")
+        return out
+
+    def get_params(self):
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _check(load().lbm_mlp_get_params(self.h, _fptr(out)), "lbm_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load().lbm_mlp_set_params(self.h, _fptr(p)), "lbm_mlp_set_params")
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 5)
+        y = np.empty(len(X), dtype=np.float32)
+        _check(load().lbm_mlp_predict(self.h, _fptr(X), len(X), _fptr(y)), "lbm_mlp_predict")
+        return y
+
+    def loss_grad(self, X, t):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 5)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = _D()
+        g = np.empty(self.num_params(), dtype=np.float32)
+        _check(load().lbm_mlp_loss_grad(self.h, _fptr(X), _fptr(t), len(X), ctypes.byref(loss), _fptr(g)),
+               "lbm_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, X, t, epochs, lr=1e-3, batch=4096):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 5)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = _D()
+        _check(load().lbm_mlp_train(self.h, _fptr(X), _fptr(t), len(X), int(epochs), float(lr), int(batch),
+                                    ctypes.byref(loss)), "lbm_mlp_train")
+        return loss.value
+
+    def save(self, path):
+        _check(load().lbm_mlp_save(self.h, path.encode()), "lbm_mlp_save")
+
+
+def lbm_init_droplet_learned(ctx, mlp, R, rho_l, rho_g, width):
+    """Returns (used_fallback, R_eff)."""
+    fb = _I()
+    reff = _D()
+    _check(load().lbm_init_droplet_learned(ctx, mlp.h, R, rho_l, rho_g, width, ctypes.byref(fb),
+                                           ctypes.byref(reff)), "lbm_init_droplet_learned")
+    return bool(fb.value), reff.value
+
+
 def lbm_strerror(code: int) -> str:
     return load().lbm_strerror(code).decode()
 
@@ -436,6 +537,9 @@ class Domain:
 
     def init_from_rho(self, rho):
         lbm_init_from_rho(self.ctx, np.asarray(rho, dtype=np.float64).reshape(-1))
+
+    def init_droplet_learned(self, mlp, R, rho_l, rho_g, width):
+        return lbm_init_droplet_learned(self.ctx, mlp, R, rho_l, rho_g, width)
 
     def get_f(self):
         out = np.empty(self.Q * self.N)

@@ -1,0 +1,109 @@
+"""The warm-start network on the GPU (BF16 tensor-core GEMMs, FP32 accumulate)
+against the FP64 reference MLP, and the learned warm start against the plain
+tanh start."""
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+
+def unpack(vec):
+    params, o = [], 0
+    for fi, fo in zip(ref.SIZES[:-1], ref.SIZES[1:]):
+        W = vec[o:o + fi * fo].astype(np.float64).reshape(fi, fo)
+        o += fi * fo
+        b = vec[o:o + fo].astype(np.float64)
+        o += fo
+        params.append((W, b))
+    assert o == len(vec)
+    return params
+
+
+def test_forward_matches_reference(lbm):
+    net = lbm.MLP(seed=11)
+    rng = np.random.default_rng(0)
+    X = rng.uniform(-1.5, 1.5, size=(3000, 5)).astype(np.float32)
+    y = net.predict(X)
+    yr, _ = ref.forward(unpack(net.get_params()), X.astype(np.float64))
+    # BF16 operands (8-bit mantissa) through four layers of 128: a few 1e-3 relative
+    err = np.abs(y - yr).max() / np.abs(yr).max()
+    assert err < 2e-2, err
+
+
+def test_gradients_match_reference(lbm):
+    net = lbm.MLP(seed=12)
+    rng = np.random.default_rng(1)
+    X = rng.uniform(-1.5, 1.5, size=(512, 5)).astype(np.float32)
+    t = rng.normal(size=512).astype(np.float32)
+    loss, g = net.loss_grad(X, t)
+    lr_, gr = ref.loss_and_grads(unpack(net.get_params()), X.astype(np.float64), t.astype(np.float64))
+    assert loss == pytest.approx(lr_, rel=2e-2)
+    o = 0
+    for (gW, gb) in gr:
+        for ref_g in (gW, gb):
+            n = ref_g.size
+            gpu = g[o:o + n].reshape(ref_g.shape)
+            o += n
+            rel = np.linalg.norm(gpu - ref_g) / max(np.linalg.norm(ref_g), 1e-30)
+            assert rel < 5e-2, (o, rel)
+    assert o == len(g)
+
+
+def test_training_fits_a_smooth_function(lbm):
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, size=(40000, 5)).astype(np.float32)
+    t = (1.0 + 0.8 * np.tanh(3 * X[:, 4]) + 0.1 * X[:, 0]).astype(np.float32)
+    net = lbm.MLP(seed=3)
+    l0, _ = net.loss_grad(X[:4096], t[:4096])
+    loss = net.train(X, t, epochs=30, lr=2e-3, batch=2048)
+    assert loss < 0.02 * l0, (l0, loss)
+    y = net.predict(X[:1000])
+    assert np.abs(y - t[:1000]).max() < 0.15
+
+
+def test_parameter_roundtrip_and_file(lbm, tmp_path):
+    net = lbm.MLP(seed=4)
+    p = net.get_params()
+    assert len(p) == 50433
+    path = str(tmp_path / "net.bin")
+    net.save(path)
+    other = lbm.MLP.load_file(path)
+    assert np.array_equal(other.get_params(), p)
+    X = np.random.default_rng(3).uniform(-1, 1, size=(100, 5)).astype(np.float32)
+    assert np.array_equal(other.predict(X), net.predict(X))
+
+
+def test_learned_warm_start_reaches_the_plain_steady_state(lbm):
+    """Train on steady droplets from a small batched sweep, then start a new
+    droplet from the network: same mass as the tanh start, same steady state
+    (max |drho| <= 1e-6, max|u| within 5%), in fewer steps than the tanh start."""
+    from paper_1906_11027_gb300 import warmstart
+    doms = []
+    rng = np.random.default_rng(7)
+    for _ in range(36):
+        doms.append(dict(nx=64, ny=64, G=float(rng.uniform(-5.4, -4.6)), tau=1.0, stencil=4,
+                         rho_l=2.0, rho_g=0.15, R=float(rng.uniform(10, 20)), width=2.0))
+    b = lbm.Batch(doms, precision=lbm.LBM_FP32_SHIFTED)
+    _, obs, _ = b.run_to_steady(1e-10, 100000, 100)
+    Xt, yt, Xv, yv, _ = warmstart.dataset_from_batch(b, doms, obs)
+    b.close()
+    net, _ = warmstart.train(Xt, yt, epochs=60)
+    assert float(np.mean((net.predict(Xv) - yv) ** 2)) < 1e-3
+    res = {}
+    for mode in ("plain", "warm"):
+        dom = lbm.Domain(64, 64, G=-5.05, tau=1.0, stencil=4)
+        if mode == "plain":
+            dom.init_droplet(2.0, 0.15, 15.5, 2.0)
+        else:
+            fb, _ = dom.init_droplet_learned(net, 15.5, 2.0, 0.15, 2.0)
+            assert not fb
+        m0 = dom.observables()["mass"]
+        steps, ok = dom.run_to_steady(1e-12, 300000, 100)
+        assert ok
+        res[mode] = (steps, m0, dom.observables()["max_u"], dom.fields()["rho"])
+    assert res["warm"][1] == pytest.approx(res["plain"][1], rel=1e-13)
+    assert np.abs(res["warm"][3] - res["plain"][3]).max() <= 1e-6
+    assert res["warm"][2] == pytest.approx(res["plain"][2], rel=0.05)
+    assert res["warm"][0] < res["plain"][0]
