@@ -158,13 +158,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest value over the ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_mlups(world, cells_per_rank, steps, max_elapsed_ms):
+    """Whole-job throughput of `world` replicas, timed by the slowest rank."""
+    return world * cells_per_rank * steps / (max_elapsed_ms * 1e-3) / 1e6
 
 
 def oracle_sample_run(wl, budget_s, steps):
@@ -252,7 +259,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     ms_per_step = elapsed_ms / args.steps
-    value = world * cells * args.steps / (elapsed_ms * 1e-3) / 1e6
+    value = job_mlups(world, cells, args.steps, elapsed_ms)
 
     # roofline of the dominant kernel
     peak, peak_src = measured_peak_gbs()

@@ -62,7 +62,9 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
+        # LBM_ORACLE_LIB: a separately compiled copy (the mutation tests plant
+        # mistakes in one and check that the pins catch them)
+        lib = ctypes.CDLL(os.environ.get("LBM_ORACLE_LIB") or build())
         V, I, D, P, L = None, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
         sig = {
             "or_create": (P, [I, I, I, I, I, I, D, D, D, I, D, D, D]),

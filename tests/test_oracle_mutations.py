@@ -1,0 +1,43 @@
+"""The pins catch plausible mistakes: each case plants one in a copy of the
+oracle's source (on the CPU), builds it, and runs the pin that must fail."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "lbm_oracle.c")
+
+MUTATIONS = [
+    ("force sign", "F[i] = -s->G * p0 * acc[i];", "F[i] = s->G * p0 * acc[i];",
+     "tests/test_oracle_force.py::test_force_on_monomials_gives_isotropic_moments"),
+    ("streaming direction", "size_t dst = cell_index(s, wrap(x + s->c[b][0], s->nx),",
+     "size_t dst = cell_index(s, wrap(x - s->c[b][0], s->nx),",
+     "tests/test_oracle_collision.py::test_streaming_is_the_shift_permutation"),
+    ("dropped u.u term of feq", " - uu / (2.0 * s->cs2));", ");",
+     "tests/test_oracle_collision.py::test_feq_moments"),
+    ("Guo prefactor", "double pref = 1.0 - 1.0 / (2.0 * s->tau);", "double pref = 1.0 - 1.0 / s->tau;",
+     "tests/test_oracle_collision.py::test_guo_forcing_moments"),
+    ("E8 weight", "s->sq[1] = 2; s->w[1] = 4.0 / 45.0;", "s->sq[1] = 2; s->w[1] = 4.0 / 44.0;",
+     "tests/test_oracle_tables.py::test_force_stencil_matches_exact_isotropy_solution"),
+    ("transposed MRT inverse", "fout[b] += s->Minv[b][k] * mpost[k];", "fout[b] += s->Minv[k][b] * mpost[k];",
+     "tests/test_oracle_collision.py::test_mrt_with_uniform_rates_is_bgk"),
+    ("half-force velocity", "u[i] = (j[i] + 0.5 * F[i]) / rho;", "u[i] = (j[i] + F[i]) / rho;",
+     "tests/test_oracle_collision.py::test_guo_forcing_moments"),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_planted_mistake(tmp_path, name, old, new, pin):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    mutated = tmp_path / "mutated.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutated.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                    "-o", str(lib), str(mutated), "-lm"], check=True)
+    env = dict(os.environ, LBM_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", pin],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pin {pin} did not catch: {name}"
