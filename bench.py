@@ -37,6 +37,9 @@ WORKLOADS = {
     "d3q19_256_fp32_iso6": dict(lattice=1, shape=(256, 256, 256), precision=1, stencil=6, R=40.0,
                                 desc="D3Q19 BGK FP32-shifted 256^3 periodic, psi=1-exp(-rho), G=-5, "
                                      "6th-order 3-D force stencil, centred droplet R=40"),
+    "d2q9_8192_fp32": dict(lattice=0, shape=(1, 8192, 8192), precision=1, stencil=4, R=2048.0,
+                           desc="D2Q9 BGK FP32-shifted 8192^2 periodic, psi=1-exp(-rho), G=-5, 4th-order stencil, "
+                                "centred droplet R=2048"),
     "d2q9_64_fp64": dict(lattice=0, shape=(1, 64, 64), precision=0, stencil=4, R=16.0,
                          desc="D2Q9 BGK FP64 64^2 periodic, psi=1-exp(-rho), G=-5, 4th-order stencil, "
                               "centred droplet R=16"),
