@@ -331,9 +331,12 @@ def run_ours(args, world, rank, local):
 
 def run_sweep(args):
     """Batched FP32 sweep (one persistent-kernel CUDA graph for all domains) against
-    plain FP64 one-domain-per-launch runs of the same domains, both to steady state."""
+    plain FP64 one-domain-per-launch runs of the same domains, both to steady state.
+    With --sweep-warm the batched arm starts every domain from the learned warm
+    start, the network trained beforehand on the steady states of a separate draw
+    of domains (another seed), so the timed domains are unseen."""
     import torch
-    from paper_1906_11027_gb300 import inputs, lbm
+    from paper_1906_11027_gb300 import inputs, lbm, warmstart
 
     lbm.load()
     doms = inputs.sweep_domains(args.sweep_domains)
@@ -344,24 +347,53 @@ def run_sweep(args):
     w.step(4)
     w.close()
     K = 100
-    t0 = time.perf_counter()
-    b = lbm.Batch(doms, precision=lbm.LBM_FP32_SHIFTED)
-    steps32, obs32, ok32 = b.run_to_steady(1e-10, args.sweep_max_steps, K)
-    # precision policy: a steady current below FP32's velocity resolution is
-    # re-converged in FP64, continued from the FP32 state
-    tiny = [i for i, o in enumerate(obs32) if np.isfinite(o["max_u"]) and o["max_u"] < args.fp64_below]
-    if tiny:
-        b64 = lbm.Batch([doms[i] for i in tiny], precision=lbm.LBM_FP64)
-        for j, i in enumerate(tiny):
-            b64.set_f(j, b.get_f(i))
-        s64, o64, _ = b64.run_to_steady(1e-10, args.sweep_max_steps, K)
-        for j, i in enumerate(tiny):
-            steps32[i] += s64[j]
-            obs32[i] = o64[j]
-        b64.close()
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    b.close()
+    net, train_info = None, None
+    if args.sweep_warm:
+        t0 = time.perf_counter()
+        tdoms = inputs.sweep_domains(args.ws_train_domains, seed=inputs.SWEEP_SEED + 1)
+        tb = lbm.Batch(tdoms, precision=lbm.LBM_FP32_SHIFTED)
+        _, tobs, _ = tb.run_to_steady(1e-10, args.sweep_max_steps, K)
+        Xt, yt, Xv, yv, _ = warmstart.dataset_from_batch(tb, tdoms, tobs)
+        tb.close()
+        t_gen = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        net, loss = warmstart.train(Xt, yt, epochs=args.ws_epochs)
+        torch.cuda.synchronize()
+        train_info = {"train_domains": len(tdoms), "train_seed": inputs.SWEEP_SEED + 1,
+                      "train_samples": int(len(yt)), "profile_sweep_s": round(t_gen, 2),
+                      "train_s": round(time.perf_counter() - t0, 2), "train_loss": loss,
+                      "val_mse": float(np.mean((net.predict(Xv) - yv) ** 2)) if len(yv) else None}
+
+    def batched_arm(warm):
+        t0 = time.perf_counter()
+        b = lbm.Batch(doms, precision=lbm.LBM_FP32_SHIFTED)
+        fallbacks = warmstart.batch_warm_init(b, doms, net) if warm else None
+        t_init = time.perf_counter() - t0
+        steps32, obs32, ok32 = b.run_to_steady(1e-10, args.sweep_max_steps, K)
+        # precision policy: a steady current below FP32's velocity resolution is
+        # re-converged in FP64, continued from the FP32 state
+        tiny = [i for i, o in enumerate(obs32) if np.isfinite(o["max_u"]) and o["max_u"] < args.fp64_below]
+        if tiny:
+            b64 = lbm.Batch([doms[i] for i in tiny], precision=lbm.LBM_FP64)
+            for j, i in enumerate(tiny):
+                b64.set_f(j, b.get_f(i))
+            s64, o64, _ = b64.run_to_steady(1e-10, args.sweep_max_steps, K)
+            for j, i in enumerate(tiny):
+                steps32[i] += s64[j]
+                obs32[i] = o64[j]
+            b64.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sched = b.schedule_report()
+        b.close()
+        return dict(t=dt, t_init=t_init, steps=steps32, obs=obs32, ok=ok32, tiny=len(tiny), fallbacks=fallbacks,
+                    schedule=sched)
+
+    plain = batched_arm(False)
+    warm = batched_arm(True) if args.sweep_warm else None
+    main_arm = warm if warm else plain
+    t_batch, steps32, obs32, ok32 = main_arm["t"], main_arm["steps"], main_arm["obs"], main_arm["ok"]
+    tiny = [None] * main_arm["tiny"]
     t0 = time.perf_counter()
     steps64, obs64 = [], []
     for d in doms:
@@ -383,10 +415,19 @@ def run_sweep(args):
     diverged = {"fp64": sum(1 for o in obs64 if not np.isfinite(o["max_u"])),
                 "batched_fp32": sum(1 for o in obs32 if not np.isfinite(o["max_u"]))}
     ratio = [abs(obs32[i]["max_u"] / obs64[i]["max_u"] - 1.0) for i in finite] or [float("nan")]
+    # max|u| below FP32 velocity resolution in both arms (dissolved droplet or a
+    # current too small to resolve): relative differences there are not physics
+    small = [i for i in finite if max(obs32[i]["max_u"], obs64[i]["max_u"]) < args.fp64_below]
+    arms = {"batched_fp32_tanh_s": round(plain["t"], 3)}
+    if warm:
+        arms.update({"batched_fp32_warm_s": round(warm["t"], 3), "warm_init_s": round(warm["t_init"], 3),
+                     "warm_fallbacks": warm["fallbacks"],
+                     "steps_total_tanh": int(sum(plain["steps"])), "steps_total_warm": int(sum(warm["steps"]))})
     line = {
         "metric": "sweep_time_to_steady_s", "value": round(t_batch, 3), "unit": "s", "higher_is_better": False,
         "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "d2q9_sweep", "domains": len(doms), "cells": cells, "seed": inputs.SWEEP_SEED,
+        "config": {"workload": "d2q9_sweep_warm" if warm else "d2q9_sweep", "domains": len(doms), "cells": cells,
+                   "seed": inputs.SWEEP_SEED, "batch_tile": main_arm["schedule"],
                    "rule": "|max|u|(t) - max|u|(t-100)| / 100 < 1e-10 (FP32 adds the floor 1e-6 max|u|/100), "
                            "checked every 100 steps in both arms",
                    "fp64_below": args.fp64_below, "promoted_to_fp64": len(tiny),
@@ -400,7 +441,12 @@ def run_sweep(args):
                         int(steps64[i]), float("%.4g" % obs32[i]["max_u"]), float("%.4g" % obs64[i]["max_u"])]
                        for i, d in enumerate(doms)] if args.sweep_details else None,
         "max_u_rel_diff": {"max": round(max(ratio), 4), "median": round(float(np.median(ratio)), 4),
-                           "within_5pct": sum(1 for r in ratio if r <= 0.05), "compared": len(finite)},
+                           "within_5pct": sum(1 for r in ratio if r <= 0.05), "compared": len(finite),
+                           "both_below_fp64_threshold": len(small),
+                           "within_5pct_or_both_below": sum(1 for i, r in zip(finite, ratio)
+                                                            if r <= 0.05 or i in small)},
+        "arms": arms,
+        "warm_start_training": train_info,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -455,16 +501,18 @@ def run_warmstart(args):
         r = compare(lambda d=d: lbm.Domain(d["nx"], d["ny"], G=d["G"], tau=d["tau"], stencil=d["stencil"]),
                     lambda dom, d=d: dom.init_droplet(d["rho_l"], d["rho_g"], d["R"], d["width"]),
                     lambda dom, d=d: dom.init_droplet_learned(net, d["R"], d["rho_l"], d["rho_g"], d["width"]),
-                    1e-12, 400000)
+                    1e-13, 600000)
         r.update(L=d["nx"], G=round(d["G"], 3), tau=d["tau"], order=d["stencil"], R=round(d["R"], 1))
         heldout.append(r)
     big2 = compare(lambda: lbm.Domain(512, 512, G=-5.0, tau=1.0, stencil=4),
                    lambda dom: dom.init_droplet(2.0, 0.15, 100.0, 2.0),
-                   lambda dom: dom.init_droplet_learned(net, 100.0, 2.0, 0.15, 2.0), 1e-12, 600000)
+                   lambda dom: dom.init_droplet_learned(net, 100.0, 2.0, 0.15, 2.0), 1e-13, 900000)
+    # FP64 in 3-D too: the 1e-6 density match needs the slow relaxation resolved
+    # below FP32's round-off floor
     big3 = compare(lambda: lbm.Domain(128, 128, 128, lattice=lbm.LBM_D3Q19, G=-5.0, tau=1.0,
-                                      precision=lbm.LBM_FP32_SHIFTED),
+                                      precision=lbm.LBM_FP64),
                    lambda dom: dom.init_droplet(2.0, 0.15, 30.0, 2.0),
-                   lambda dom: dom.init_droplet_learned(net, 30.0, 2.0, 0.15, 2.0), 1e-10, 200000)
+                   lambda dom: dom.init_droplet_learned(net, 30.0, 2.0, 0.15, 2.0), 1e-13, 400000)
     used = [h for h in heldout if not h["fallback"]]
     line = {
         "metric": "warm_start_steps_saved", "unit": "fraction of plain steps",
@@ -473,7 +521,8 @@ def run_warmstart(args):
         "config": {"workload": "learned_warm_start", "sweep_domains": len(doms), "train_samples": int(len(yt)),
                    "val_samples": int(len(yv)), "heldout_domains": len(held), "epochs": args.ws_epochs},
         "sweep_s": round(t_sweep, 2), "train_s": round(t_train, 2), "train_loss": loss, "val_mse": val_mse,
-        "heldout": heldout, "d2q9_512": big2, "d3q19_128_fp32": big3,
+        "steady_rule": "|max|u|(t) - max|u|(t-100)| / 100 < 1e-13, FP64 runs",
+        "heldout": heldout, "d2q9_512": big2, "d3q19_128_fp64": big3,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -492,6 +541,9 @@ def main():
     ap.add_argument("--sweep-domains", type=int, default=64)
     ap.add_argument("--sweep-max-steps", type=int, default=200000)
     ap.add_argument("--sweep-details", action="store_true")
+    ap.add_argument("--sweep-warm", action="store_true",
+                    help="batched arm starts from the learned warm start (network trained first on another draw)")
+    ap.add_argument("--ws-train-domains", type=int, default=128)
     ap.add_argument("--warmstart", action="store_true", help="train and evaluate the learned warm start")
     ap.add_argument("--ws-epochs", type=int, default=80)
     ap.add_argument("--ws-heldout", type=int, default=12)

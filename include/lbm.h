@@ -241,6 +241,18 @@ int lbm_batch_observables(lbm_batch* b, lbm_obs* obs_per_domain);
 int lbm_batch_get_populations(lbm_batch* b, int d, double* f_host);
 int lbm_batch_set_populations(lbm_batch* b, int d, const double* f_host);
 
+/* Tile shape of the batch step kernel (cells per tile along x by rows per work
+ * item).  The first lbm_batch_step / lbm_batch_run_to_steady (or this call) times
+ * every compiled shape for a few steps on the batch's current state, restores the
+ * state, and keeps the fastest; all shapes perform the same per-cell arithmetic,
+ * so results are bitwise the same whichever is chosen.  The report is
+ * "chosen=NAME;NAME=ms;..." in buf (NUL-terminated, truncated to len). */
+int lbm_batch_schedule_report(lbm_batch* b, char* buf, int len);
+
+/* Pins the tile shape to the named one (a name the report lists), skipping the
+ * autotuner; LBM_EINVAL for an unknown name. */
+int lbm_batch_set_schedule(lbm_batch* b, const char* name);
+
 /* ---- learned warm start ------------------------------------------------------ */
 
 /* A multilayer perceptron 5 -> 128 -> 128 -> 128 -> 128 -> 1 with SiLU activations

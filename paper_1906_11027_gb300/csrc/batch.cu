@@ -3,7 +3,10 @@
 // kernel per step, captured in a CUDA graph together with a per-domain steady
 // check; converged domains retire and drop out of the work list.
 //
-// Work item = (domain, tile of TX cells along x, chunk of ZC rows along y).  Each
+// Work item = (domain, tile of TX cells along x, chunk of ZC rows along y); the
+// tile width and chunk length are picked per batch by an autotuner that times
+// each compiled shape on the batch's own domains (all shapes perform the same
+// per-cell arithmetic, so the choice changes speed only).  Each
 // item runs the one-pass march of the single-domain kernels: psi of the tile and
 // its halo is formed one row ahead into a shared-memory ring, the populations
 // wait in a shared-memory stash, then force (Eq. 1), Guo-forced BGK collision
@@ -16,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -25,11 +29,8 @@
 namespace lbm {
 namespace {
 
-constexpr int kBTX = 64;   // tile width (threads per CTA)
-constexpr int kBZC = 16;   // rows per chunk
 constexpr int kBMaxR = 3;  // largest stencil radius (10th order)
 constexpr int kBNS = 2 * kBMaxR + 2;
-constexpr int kBEX = kBTX + 2 * kBMaxR;
 constexpr int kQ9 = 9;
 
 struct BatchDom {
@@ -55,7 +56,7 @@ __device__ __forceinline__ DevParams dom_params(const BatchDom& d)
 
 // One (tile, chunk) of one domain: the 2-D one-pass march with a shared-memory
 // stash.  ring: [NS][EX] psi, stash: [R + 1][Q][TX] populations.
-template <int ORD, class Real>
+template <int ORD, class Real, int TX, int ZC>
 __device__ void batch_item(const Real* __restrict__ A, Real* __restrict__ Bo, const DevParams& p, int x0, int m0,
                            Real* ring, Real* stash)
 {
@@ -64,7 +65,6 @@ __device__ void batch_item(const Real* __restrict__ A, Real* __restrict__ Bo, co
     constexpr int R = S::radius;
     constexpr int RE = 1;
     constexpr int Q = kQ9;
-    constexpr int TX = kBTX;
     constexpr int EX = TX + 2 * R;
     constexpr int E = EX;
     constexpr int NS = 2 * R + 2;
@@ -76,7 +76,7 @@ __device__ void batch_item(const Real* __restrict__ A, Real* __restrict__ Bo, co
         P.out[b] = Bo + static_cast<long long>(b) * p.N;
     }
     const int nm = p.ny;
-    const int m1 = (m0 + kBZC < nm) ? m0 + kBZC : nm;
+    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
     const int tid = threadIdx.x;
     const int ix = x0 + tid;
     int ixo[2 * RE + 1];
@@ -135,13 +135,13 @@ __device__ void batch_item(const Real* __restrict__ A, Real* __restrict__ Bo, co
 }
 
 // Persistent step kernel: every CTA walks the work list with stride gridDim.x.
-template <class Real>
-__global__ void __launch_bounds__(kBTX) k_batch_step(const BatchDom* __restrict__ doms, const int4* __restrict__ items,
-                                                    const int* __restrict__ nitems, const Real* __restrict__ pool_in,
-                                                    Real* __restrict__ pool_out)
+template <class Real, int TX, int ZC>
+__global__ void __launch_bounds__(TX) k_batch_step(const BatchDom* __restrict__ doms, const int4* __restrict__ items,
+                                                   const int* __restrict__ nitems, const Real* __restrict__ pool_in,
+                                                   Real* __restrict__ pool_out)
 {
-    __shared__ Real ring[kBNS * kBEX];
-    __shared__ Real stash[(kBMaxR + 1) * kQ9 * kBTX];
+    __shared__ Real ring[kBNS * (TX + 2 * kBMaxR)];
+    __shared__ Real stash[(kBMaxR + 1) * kQ9 * TX];
     const int n = *nitems;
     for (int it = blockIdx.x; it < n; it += gridDim.x) {
         const int4 w = items[it];
@@ -149,12 +149,12 @@ __global__ void __launch_bounds__(kBTX) k_batch_step(const BatchDom* __restrict_
         const DevParams p = dom_params(d);
         const Real* A = pool_in + d.off;
         Real* Bo = pool_out + d.off;
-        const int x0 = w.y * kBTX, m0 = w.z * kBZC;
+        const int x0 = w.y * TX, m0 = w.z * ZC;
         switch (d.order) {
-        case 4: batch_item<4, Real>(A, Bo, p, x0, m0, ring, stash); break;
-        case 6: batch_item<6, Real>(A, Bo, p, x0, m0, ring, stash); break;
-        case 8: batch_item<8, Real>(A, Bo, p, x0, m0, ring, stash); break;
-        default: batch_item<10, Real>(A, Bo, p, x0, m0, ring, stash); break;
+        case 4: batch_item<4, Real, TX, ZC>(A, Bo, p, x0, m0, ring, stash); break;
+        case 6: batch_item<6, Real, TX, ZC>(A, Bo, p, x0, m0, ring, stash); break;
+        case 8: batch_item<8, Real, TX, ZC>(A, Bo, p, x0, m0, ring, stash); break;
+        default: batch_item<10, Real, TX, ZC>(A, Bo, p, x0, m0, ring, stash); break;
         }
         __syncthreads();  // shared memory is reused by the next item
     }
@@ -362,6 +362,9 @@ struct lbm_batch {
     cudaGraphExec_t graph[2];
     int graph_k;
     int graph_cur;  // parity the graph was captured from
+    int var;        // tile shape in use (index into the variant table)
+    bool tuned;     // autotuner has run, or a shape was pinned
+    std::vector<double> tune_ms;  // ms per step of each shape (< 0: not timed)
 
     void* dalloc(size_t bytes)
     {
@@ -385,6 +388,52 @@ struct lbm_batch {
 
 namespace {
 
+// Compiled tile shapes of the batch step kernel: TX cells per tile (= threads per
+// CTA) by ZC rows per work item.
+struct BatchVariant {
+    const char* name;
+    int tx, zc;
+    cudaError_t (*launch)(lbm_batch* b, int parity);
+    int (*occupancy)(int fp32);
+};
+
+template <int TX, int ZC>
+cudaError_t launch_variant(lbm_batch* b, int parity)
+{
+    if (b->fp32)
+        k_batch_step<float, TX, ZC><<<b->grid, TX, 0, b->stream>>>(
+            b->d_doms, b->d_items, b->d_nitems, static_cast<const float*>(b->pool[parity]),
+            static_cast<float*>(b->pool[parity ^ 1]));
+    else
+        k_batch_step<double, TX, ZC><<<b->grid, TX, 0, b->stream>>>(
+            b->d_doms, b->d_items, b->d_nitems, static_cast<const double*>(b->pool[parity]),
+            static_cast<double*>(b->pool[parity ^ 1]));
+    return cudaGetLastError();
+}
+
+template <int TX, int ZC>
+int occupancy_variant(int fp32)
+{
+    int occ = 0;
+    if (fp32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_step<float, TX, ZC>, TX, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_step<double, TX, ZC>, TX, 0);
+    return occ;
+}
+
+const BatchVariant kBatchVariants[] = {
+    {"tile64_rows16", 64, 16, &launch_variant<64, 16>, &occupancy_variant<64, 16>},
+    {"tile32_rows16", 32, 16, &launch_variant<32, 16>, &occupancy_variant<32, 16>},
+    {"tile32_rows32", 32, 32, &launch_variant<32, 32>, &occupancy_variant<32, 32>},
+    {"tile64_rows8", 64, 8, &launch_variant<64, 8>, &occupancy_variant<64, 8>},
+    {"tile64_rows32", 64, 32, &launch_variant<64, 32>, &occupancy_variant<64, 32>},
+    {"tile128_rows16", 128, 16, &launch_variant<128, 16>, &occupancy_variant<128, 16>},
+    {"tile128_rows32", 128, 32, &launch_variant<128, 32>, &occupancy_variant<128, 32>},
+};
+constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
+constexpr int kMinTX = 32, kMinZC = 8;  // smallest tile and chunk of the table (item buffer size)
+
 #define LBM_BCK(call)                                                                                  \
     do {                                                                                               \
         cudaError_t e_ = (call);                                                                       \
@@ -397,11 +446,15 @@ namespace {
 
 int rebuild_items(lbm_batch* b)
 {
+    const BatchVariant& v = kBatchVariants[b->var];
     std::vector<int4> items;
     for (int d = 0; d < b->n; ++d) {
-        if (!b->doms[d].active) continue;
-        for (int c = 0; c < b->doms[d].nch; ++c)
-            for (int t = 0; t < b->doms[d].ntx; ++t) items.push_back(make_int4(d, t, c, 0));
+        BatchDom& m = b->doms[d];
+        m.ntx = (m.nx + v.tx - 1) / v.tx;
+        m.nch = (m.ny + v.zc - 1) / v.zc;
+        if (!m.active) continue;
+        for (int c = 0; c < m.nch; ++c)
+            for (int t = 0; t < m.ntx; ++t) items.push_back(make_int4(d, t, c, 0));
     }
     b->nitems = static_cast<int>(items.size());
     if (!items.empty())
@@ -414,15 +467,68 @@ int rebuild_items(lbm_batch* b)
 
 cudaError_t launch_step(lbm_batch* b, int parity)
 {
-    if (b->fp32)
-        k_batch_step<float><<<b->grid, kBTX, 0, b->stream>>>(
-            b->d_doms, b->d_items, b->d_nitems, static_cast<const float*>(b->pool[parity]),
-            static_cast<float*>(b->pool[parity ^ 1]));
-    else
-        k_batch_step<double><<<b->grid, kBTX, 0, b->stream>>>(
-            b->d_doms, b->d_items, b->d_nitems, static_cast<const double*>(b->pool[parity]),
-            static_cast<double*>(b->pool[parity ^ 1]));
-    return cudaGetLastError();
+    return kBatchVariants[b->var].launch(b, parity);
+}
+
+// Makes shape v current: persistent grid = SMs x resident CTAs, work list rebuilt,
+// captured graphs dropped (they hold the previous kernel).
+int select_variant(lbm_batch* b, int v)
+{
+    b->var = v;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    b->grid = std::max(1, nsm * std::max(1, kBatchVariants[v].occupancy(b->fp32)));
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) {
+            cudaGraphExecDestroy(b->graph[k]);
+            b->graph[k] = nullptr;
+        }
+    return rebuild_items(b);
+}
+
+// Times every shape on the batch's current state (a few steps each, from a saved
+// copy that is put back afterwards, so the state does not advance) and keeps the
+// fastest.  Without room for the copy the default shape stays.
+int autotune(lbm_batch* b)
+{
+    if (b->tuned) return LBM_OK;
+    b->tuned = true;
+    const size_t bytes = (b->fp32 ? 4 : 8) * static_cast<size_t>(b->pool_elems);
+    void* save = b->dalloc(bytes);
+    if (!save) return LBM_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LBM_OK;
+    auto ck = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == LBM_OK) rc = set_last_error(LBM_ECUDA, cudaGetErrorString(e));
+    };
+    ck(cudaEventCreate(&e0));
+    ck(cudaEventCreate(&e1));
+    ck(cudaMemcpyAsync(save, b->pool[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
+    constexpr int kWarm = 2, kTimed = 8;
+    b->tune_ms.assign(kNumBatchVariants, -1.0);
+    int best = 0;
+    for (int v = 0; v < kNumBatchVariants && rc == LBM_OK; ++v) {
+        if (int r = select_variant(b, v)) {
+            rc = r;
+            break;
+        }
+        for (int i = 0; i < kWarm; ++i) ck(launch_step(b, (b->cur + i) & 1));
+        ck(cudaEventRecord(e0, b->stream));
+        for (int i = 0; i < kTimed; ++i) ck(launch_step(b, (b->cur + kWarm + i) & 1));
+        ck(cudaEventRecord(e1, b->stream));
+        ck(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ck(cudaEventElapsedTime(&ms, e0, e1));
+        b->tune_ms[v] = ms / kTimed;
+        if (b->tune_ms[v] < b->tune_ms[best]) best = v;
+        ck(cudaMemcpyAsync(b->pool[b->cur], save, bytes, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    ck(cudaStreamSynchronize(b->stream));
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->dfree(save);
+    if (rc != LBM_OK) return rc;
+    return select_variant(b, best);
 }
 
 // Observables of every domain into d_res (the state pointed to by d_cur_of).
@@ -496,8 +602,8 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
         m.nx = p.nx;
         m.ny = p.ny;
         m.order = p.stencil == LBM_STENCIL_LATTICE ? 4 : p.stencil;
-        m.ntx = (p.nx + kBTX - 1) / kBTX;
-        m.nch = (p.ny + kBZC - 1) / kBZC;
+        m.ntx = (p.nx + kMinTX - 1) / kMinTX;  // item buffer sized for the finest shape
+        m.nch = (p.ny + kMinZC - 1) / kMinZC;
         m.active = 1;
         m.off = off;
         m.G = p.G;
@@ -567,14 +673,7 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
     else
         k_batch_init<double><<<g, 256, 0, b->stream>>>(b->d_doms, b->d_init, n, static_cast<double*>(b->pool[0]));
     ck(cudaGetLastError());
-    int nsm = 0, occ = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
-    if (fp32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_step<float>, kBTX, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_step<double>, kBTX, 0);
-    b->grid = std::max(1, nsm * std::max(1, occ));
-    if (rc == LBM_OK) rc = rebuild_items(b);
+    if (rc == LBM_OK) rc = select_variant(b, 0);
     if (rc != LBM_OK) {
         lbm_batch_destroy(b);
         return rc;
@@ -612,6 +711,8 @@ int lbm_batch_step(lbm_batch* b, int64_t n)
 {
     if (!b || n < 0) return set_last_error(LBM_EINVAL, "lbm_batch_step: bad argument");
     LBM_BCK(cudaSetDevice(b->device));
+    if (n > 0)
+        if (int rc = autotune(b)) return rc;
     for (int64_t i = 0; i < n; ++i) {
         LBM_BCK(launch_step(b, b->cur));
         b->cur ^= 1;
@@ -632,6 +733,7 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t
     if (!b || !(tol > 0.0) || max_steps < 0 || check_every < 2 || check_every % 2)
         return set_last_error(LBM_EINVAL, "lbm_batch_run_to_steady: bad argument (check_every must be even)");
     LBM_BCK(cudaSetDevice(b->device));
+    if (int rc = autotune(b)) return rc;
     const int K = static_cast<int>(check_every);
     const double floor_rel = b->fp32 ? 1e-6 : 0.0;
     // one graph per starting parity is not needed: K is even, so every block of K
@@ -713,6 +815,34 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t
         }
     }
     return nactive == 0 ? LBM_OK : set_last_error(LBM_ENOTCONVERGED, "some domains still changing at max_steps");
+}
+
+int lbm_batch_schedule_report(lbm_batch* b, char* buf, int len)
+{
+    if (!b || !buf || len < 1) return set_last_error(LBM_EINVAL, "lbm_batch_schedule_report: bad argument");
+    LBM_BCK(cudaSetDevice(b->device));
+    if (int rc = autotune(b)) return rc;
+    std::string s = std::string("chosen=") + kBatchVariants[b->var].name;
+    for (int v = 0; v < kNumBatchVariants && v < (int)b->tune_ms.size(); ++v) {
+        if (b->tune_ms[v] < 0) continue;
+        char t[96];
+        std::snprintf(t, sizeof(t), ";%s=%.5f", kBatchVariants[v].name, b->tune_ms[v]);
+        s += t;
+    }
+    std::snprintf(buf, len, "%s", s.c_str());
+    return LBM_OK;
+}
+
+int lbm_batch_set_schedule(lbm_batch* b, const char* name)
+{
+    if (!b || !name) return set_last_error(LBM_EINVAL, "lbm_batch_set_schedule: bad argument");
+    LBM_BCK(cudaSetDevice(b->device));
+    for (int v = 0; v < kNumBatchVariants; ++v)
+        if (std::strcmp(kBatchVariants[v].name, name) == 0) {
+            b->tuned = true;
+            return select_variant(b, v);
+        }
+    return set_last_error(LBM_EINVAL, "lbm_batch_set_schedule: unknown tile shape");
 }
 
 // Observables of every domain in its current state.

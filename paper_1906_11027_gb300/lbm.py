@@ -102,6 +102,8 @@ _SIGNATURES = {
     "lbm_batch_observables": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_batch_get_populations": (_I, [_P, _I, _dp]),
     "lbm_batch_set_populations": (_I, [_P, _I, _dp]),
+    "lbm_batch_schedule_report": (_I, [_P, ctypes.c_char_p, _I]),
+    "lbm_batch_set_schedule": (_I, [_P, ctypes.c_char_p]),
     "lbm_mlp_create": (_I, [ctypes.POINTER(_P), ctypes.c_uint64]),
     "lbm_mlp_destroy": (_I, [_P]),
     "lbm_mlp_num_params": (_I, []),
@@ -320,6 +322,21 @@ def lbm_batch_set_populations(b, d, f) -> None:
     _check(load().lbm_batch_set_populations(b, int(d), _dptr(f)), "lbm_batch_set_populations")
 
 
+def lbm_batch_schedule_report(b) -> dict:
+    """{'chosen': name, name: ms per step, ...} of the batch tile-shape autotuner."""
+    buf = ctypes.create_string_buffer(4096)
+    _check(load().lbm_batch_schedule_report(b, buf, 4096), "lbm_batch_schedule_report")
+    out = {}
+    for item in buf.value.decode().split(";"):
+        k, v = item.split("=")
+        out[k] = v if k == "chosen" else float(v)
+    return out
+
+
+def lbm_batch_set_schedule(b, name: str) -> None:
+    _check(load().lbm_batch_set_schedule(b, name.encode()), "lbm_batch_set_schedule")
+
+
 class Batch:
     """Owner of one lbm_batch: domains = list of dicts with nx, ny, G, tau,
     stencil, rho_l, rho_g, R, width."""
@@ -371,6 +388,12 @@ class Batch:
 
     def set_f(self, d, f):
         lbm_batch_set_populations(self.h, d, f)
+
+    def schedule_report(self):
+        return lbm_batch_schedule_report(self.h)
+
+    def set_schedule(self, name):
+        lbm_batch_set_schedule(self.h, name)
 
 
 _fptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))  # noqa: E731

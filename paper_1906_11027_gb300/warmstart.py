@@ -70,3 +70,19 @@ def train(Xt, yt, epochs=40, lr=2e-3, batch=4096, seed=1906):
     loss = net.train(Xt, yt, epochs=max(1, epochs // 2), lr=lr, batch=batch)
     loss = net.train(Xt, yt, epochs=max(1, epochs - epochs // 2), lr=lr / 4, batch=batch)
     return net, loss
+
+
+def batch_warm_init(batch, domains, net):
+    """Replace the tanh start of every batch domain by the learned warm start (mass
+    matched to the tanh start; the tanh start stays where the library falls back).
+    Returns the number of domains that kept the tanh start."""
+    fallbacks = 0
+    for i, d in enumerate(domains):
+        dom = lbm.Domain(d["nx"], d["ny"], G=d["G"], tau=d["tau"], stencil=d["stencil"], precision=lbm.LBM_FP64)
+        fb, _ = dom.init_droplet_learned(net, d["R"], d["rho_l"], d["rho_g"], d["width"])
+        if fb:
+            fallbacks += 1
+        else:
+            batch.set_f(i, dom.get_f())
+        dom.close()
+    return fallbacks

@@ -111,3 +111,32 @@ def test_batch_retires_diverged_domain(lbm):
     assert ok
     assert obs[0]["max_u"] == float("inf")
     assert np.isfinite(obs[1]["max_u"]) and obs[1]["max_u"] < 1e-2
+
+
+def test_batch_autotuner_reports_and_every_shape_is_bitwise_equal(lbm):
+    """The tile shapes perform the same per-cell arithmetic: every shape gives
+    the same bits after the same steps, and the autotuner (which times them on a
+    saved copy of the state) leaves the state where it was."""
+    rep = None
+    outs = {}
+    b = lbm.Batch(DOMAINS, precision=1)
+    rep = b.schedule_report()
+    assert rep["chosen"] in rep and len(rep) >= 5
+    b.step(17)
+    outs["auto"] = [b.get_f(i) for i in range(len(DOMAINS))]
+    b.close()
+    for name in [k for k in rep if k != "chosen"]:
+        b = lbm.Batch(DOMAINS, precision=1)
+        b.set_schedule(name)
+        b.step(17)
+        outs[name] = [b.get_f(i) for i in range(len(DOMAINS))]
+        b.close()
+    for name, fs in outs.items():
+        for a, c in zip(fs, outs["auto"]):
+            assert np.array_equal(a, c), name
+    ref = oracle_run(DOMAINS[1], 17)
+    assert np.abs(outs["auto"][1] - ref.get_f()).max() <= 1e-5 * np.abs(ref.get_f()).max()
+    b = lbm.Batch(DOMAINS[:1], precision=0)
+    with pytest.raises(lbm.LbmError):
+        b.set_schedule("no_such_shape")
+    b.close()
