@@ -452,7 +452,9 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     if (p->path != LBM_PATH_ONE_PASS) c->cand[c->n_cand++] = -1;
     if (p->path != LBM_PATH_TWO_PASS)
         for (int v = 0; v < ks.n_onepass; ++v)
-            if (!ks.onepass[v].needs_even_nx || p->nx % 2 == 0) c->cand[c->n_cand++] = v;
+            if (p->nx % ks.onepass[v].nx_multiple == 0 &&
+                (ks.onepass[v].nx_exact == 0 || ks.onepass[v].nx_exact == p->nx))
+                c->cand[c->n_cand++] = v;
     if (c->n_cand == 0) {
         delete c;
         return fail(LBM_EUNSUPPORTED, "no one-pass variant applies to this domain");

@@ -59,7 +59,8 @@ struct LaunchArgs {
 struct StepVariant {
     const char* name;
     cudaError_t (*fn)(const LaunchArgs&, cudaStream_t);
-    bool needs_even_nx;  // two cells per thread along x
+    int nx_multiple;     // nx must be a multiple of this (two cells per thread, 16-byte rows)
+    int nx_exact;        // nonzero: the variant is compiled for this nx only (whole rows in shared memory)
 };
 constexpr int kMaxVariants = 32;
 

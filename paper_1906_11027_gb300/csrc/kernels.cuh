@@ -81,6 +81,18 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// Bulk global -> shared copy of `bytes` (16-byte aligned ends, multiple of 16)
+// counted on an mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Orders this thread's earlier generic shared-memory accesses before its later
+// async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Asynchronous 4-byte global -> shared copies (cp.async, completion by groups).
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src)
 {
@@ -630,6 +642,169 @@ __global__ void __launch_bounds__(TX * TY, MINB)
             for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
         }
     }
+}
+
+// One-pass schedule for domains whose x-row fits in shared memory (3-D,
+// radius-1 stencils): a tile is TY whole rows, so direction b's staged rows for
+// slab s -- rows y0 - 1 - c_by .. y0 + TY - c_by of plane s - c_bz, all NX cells --
+// are one contiguous range of global memory, copied by one cp.async.bulk (two
+// where the range wraps in y).  The periodic x shift becomes an index wrap in
+// shared memory, and the psi ring carries one wrapped column on each side.
+// NSTG stages are in flight; the interior populations wait one slab in registers.
+template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int ZC, int NSTG>
+__global__ void __launch_bounds__(NX * TY, 1)
+    k_onepass_row(const __grid_constant__ Pops<Real, Lattice<LAT>::Q> P, DevParams p)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<3, ORD>;
+    constexpr int R = S::radius;
+    constexpr int Q = L::Q;
+    static_assert(L::D == 3 && R == 1 && L::reach == 1, "row staging is written for 3-D radius-1 stencils");
+    constexpr int NT = NX * TY;
+    constexpr int EY = TY + 2 * R;
+    constexpr int EX = NX + 2 * R;   // ring row: one wrapped psi column on each side
+    constexpr int E = EX * EY;
+    constexpr int NS = 2 * R + 2;
+    constexpr int STG = Q * EY * NX;  // values per stage: [Q][EY][NX]
+    static_assert(NT % 32 == 0 && NT <= 1024, "block");
+    static_assert((NX * sizeof(Real)) % 16 == 0, "16-byte rows");
+    __shared__ Real ring[NS * E];
+    __shared__ alignas(8) unsigned long long bars[NSTG];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    Real* stage = reinterpret_cast<Real*>(dyn_smem);  // [NSTG][STG]
+
+    const int nty = (p.ny + TY - 1) / TY;
+    const int trow = blockIdx.x % nty;
+    const int chunk = blockIdx.x / nty;
+    const int y0 = trow * TY;
+    const int nm = p.nz;
+    const int m0 = chunk * ZC;
+    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const int plane = NX * p.ny;
+    const int tid = threadIdx.x;
+    const int tx = tid % NX, ty = tid / NX;
+    const int lane = tid & 31;
+    const bool issuer = tid < 32;
+
+    if (tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    int cby = 0, cbz = 0;
+    const Real* src_b = nullptr;
+    sfor<Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int vy = L::T.v[b][1], vz = L::T.v[b][2];
+        if (lane == b) {
+            cby = vy;
+            cbz = vz;
+            src_b = P.in[b];
+        }
+    });
+    const int base = m0 - R;
+    auto issue = [&](int s) {
+        const int slot = (s - base) % NSTG;
+        const uint32_t bar = smem_u32(&bars[slot]);
+        if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(STG * sizeof(Real)));
+        __syncwarp();
+        if (lane < Q) {
+            fence_proxy_async_smem();
+            const Real* pl = src_b + static_cast<long long>(wrap_any(s - cbz, nm)) * plane;
+            uint32_t dst = smem_u32(stage + slot * STG + lane * (EY * NX));
+            int y = y0 - R - cby, left = EY;
+            while (left > 0) {
+                const int yw = wrap_any(y, p.ny);
+                const int n = (p.ny - yw < left) ? p.ny - yw : left;
+                bulk_g2s(dst, pl + static_cast<long long>(yw) * NX, static_cast<uint32_t>(n * NX * sizeof(Real)), bar);
+                dst += static_cast<uint32_t>(n * NX * sizeof(Real));
+                y += n;
+                left -= n;
+            }
+        }
+    };
+    uint32_t phase = 0;
+    bool ok = true;
+    auto wait_stage = [&](int s) -> const Real* {
+        const int slot = (s - base) % NSTG;
+        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        phase ^= 1u << slot;
+        return stage + slot * STG;
+    };
+
+    // stage column of x - c_x for c_x = -1 and +1 (x periodic within the row)
+    const int xm = (tx + 1 == NX) ? 0 : tx + 1;   // c_x = -1
+    const int xp = (tx == 0) ? NX - 1 : tx - 1;   // c_x = +1
+    // f of the cell in frame row fy of the stage (pull: row fy of direction b)
+    auto load_cell = [&](const Real* st, int fy, Real (&f)[Q]) {
+        const Real* r = st + fy * NX;
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int vx = L::T.v[b][0];
+            const int c = vx == 0 ? tx : (vx > 0 ? xp : xm);
+            f[b] = r[b * (EY * NX) + c];
+        });
+    };
+    auto rho_psi = [&](const Real (&f)[Q]) {
+        Real sum = Real(0);
+        sfor<Q>([&](auto bI) { sum += f[decltype(bI)::value]; });
+        const Real rho = std::is_same<Real, float>::value ? Real(p.rho_bar) + sum : sum;
+        return psi_of<LAT>(rho, p);
+    };
+    Real fcur[Q], fnxt[Q];
+    auto put_psi = [&](Real* dst, int fy, Real v) {
+        Real* row = dst + fy * EX;
+        row[tx + R] = v;
+        if (tx == 0) row[NX + R] = v;       // wrapped column right of the row
+        if (tx == NX - 1) row[0] = v;       // wrapped column left of the row
+    };
+    auto psi_slab = [&](int s) {
+        const Real* st = wait_stage(s);
+        Real* dst = ring + ring_slot(s, NS) * E;
+        load_cell(st, ty + R, fnxt);
+        put_psi(dst, ty + R, rho_psi(fnxt));
+        // halo rows of the frame: fy = 0 and fy = EY - 1, NX cells each
+        for (int k = ty; k < 2 * R; k += TY) {
+            const int fy = (k < R) ? k : EY - 2 * R + k;
+            Real f[Q];
+            load_cell(st, fy, f);
+            put_psi(dst, fy, rho_psi(f));
+        }
+    };
+
+    int next = base;
+    const int last = m1 - 1 + R;
+    if (issuer)
+        for (; next <= last && next < base + NSTG; ++next) issue(next);
+    for (int s = m0 - R; s < m0 + R; ++s) psi_slab(s);
+#pragma unroll
+    for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+    __syncthreads();
+    if (issuer)
+        for (; next <= last && next < m0 + R + NSTG; ++next) issue(next);
+
+    const bool active = (y0 + ty) < p.ny;
+    const int cell_xy = (y0 + ty) * NX + tx;
+    for (int m = m0; m < m1; ++m) {
+        psi_slab(m + R);
+        __syncthreads();
+        if (issuer)
+            for (; next <= last && next <= m + R + NSTG; ++next) issue(next);
+        if (active) {
+            Real F[3];
+            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, ty + R, p.G, F);
+            collide<LAT, COLL>(fcur, F, p);
+            const int c = m * plane + cell_xy;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                P.out[b][c] = fcur[b];
+            });
+        }
+#pragma unroll
+        for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+    }
+    if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
 }
 
 // One-pass schedule with asynchronous staging (FP32 hot path): the populations
@@ -1487,6 +1662,25 @@ cudaError_t launch_onepass(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int ZC, int NSTG>
+cudaError_t launch_onepass_row(const LaunchArgs& a, cudaStream_t s)
+{
+    constexpr size_t dyn = sizeof(Real) * NSTG * Lattice<LAT>::Q * (TY + 2) * NX;
+    auto kern = &k_onepass_row<LAT, ORD, COLL, Real, NX, TY, ZC, NSTG>;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.p.nx != NX) return cudaErrorInvalidValue;
+    const int nty = (a.p.ny + TY - 1) / TY;
+    const long long nblocks = static_cast<long long>(nty) * ((a.p.nz + ZC - 1) / ZC);
+    const auto P = make_pops<Real, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
+    kern<<<static_cast<unsigned>(nblocks), NX * TY, dyn, s>>>(P, a.p);
+    return cudaGetLastError();
+}
+
 template <int LAT, int ORD, int COLL, class Real, int TX, int TY, int ZC, int MINB>
 cudaError_t launch_onepass_async(const LaunchArgs& a, cudaStream_t s)
 {
@@ -1643,11 +1837,13 @@ KernelSet make_set()
     // One-pass variants timed by the autotuner: tile TX x TY (2-D: TX), chunk of
     // ZC slabs, at least MINB resident blocks per SM (a register cap).
     k.n_onepass = 0;
-    auto add = [&k](const char* name, cudaError_t (*fn)(const LaunchArgs&, cudaStream_t), bool even_nx = false) {
+    auto add = [&k](const char* name, cudaError_t (*fn)(const LaunchArgs&, cudaStream_t), int nx_mult = 1,
+                    int nx_exact = 0) {
         if (k.n_onepass >= kMaxVariants) return;  // table full: later variants are not offered
         k.onepass[k.n_onepass].name = name;
         k.onepass[k.n_onepass].fn = fn;
-        k.onepass[k.n_onepass].needs_even_nx = even_nx;
+        k.onepass[k.n_onepass].nx_multiple = nx_mult;
+        k.onepass[k.n_onepass].nx_exact = nx_exact;
         ++k.n_onepass;
     };
     constexpr bool r1 = Stencil<Lattice<LAT>::D, ORD>::radius == 1;
@@ -1666,7 +1862,11 @@ KernelSet make_set()
             if constexpr (r1) {
                 add("onepass_async_64x4_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 64, 4, 16, 2>);
                 add("onepass_64x4_z16_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 16, 4, 2>);
-                add("onepass_x2_64x8_z16_b2_reg", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 1>, true);
+                add("onepass_row256x2_z32_s2", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 32, 2>, 1, 256);
+                add("onepass_row256x2_z64_s2", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 64, 2>, 1, 256);
+                add("onepass_row256x1_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 1, 32, 3>, 1, 256);
+                add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3>, 1, 128);
+                add("onepass_x2_64x8_z16_b2_reg", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 1>, 2);
                 add("onepass_128x4_z16_b2_smem", &launch_onepass<LAT, ORD, COLL, Real, 128, 4, 16, 2, 2>);
                 add("onepass_64x4_z8_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 8, 4, 2>);
                 add("onepass_64x4_z32_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 32, 4, 2>);
@@ -1677,7 +1877,7 @@ KernelSet make_set()
             }
             add("onepass_la_32x8_z16_b2", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 2, 1>);
             add("onepass_lai_32x8_z16_b3", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 3, 0>);
-            add("onepass_x2_64x8_z16_b2_smem", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 2>, true);
+            add("onepass_x2_64x8_z16_b2_smem", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 2>, 2);
             if constexpr (r1) {
             }
         }
@@ -1687,7 +1887,7 @@ KernelSet make_set()
             add("onepass_256_z16_b3_smem", &launch_onepass<LAT, ORD, COLL, Real, 256, 1, 16, 3, 2>);
             if constexpr (r1) add("onepass_256_z16_b3_reg", &launch_onepass<LAT, ORD, COLL, Real, 256, 1, 16, 3, 1>);
             add("onepass_async_256_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 256, 1, 16, 2>);
-            add("onepass_x2_256_z16_b2_smem", &launch_onepass_x2<LAT, ORD, 128, 1, 16, 2, 2>, true);
+            add("onepass_x2_256_z16_b2_smem", &launch_onepass_x2<LAT, ORD, 128, 1, 16, 2, 2>, 2);
         }
     }
     k.obs = &launch_obs<LAT, ORD, Real>;

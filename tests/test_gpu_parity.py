@@ -284,6 +284,8 @@ def test_one_pass_ragged_3d_against_oracle(lbm):
 
 @pytest.mark.parametrize("lattice,shape,stencil,precision", [
     (1, (40, 24, 70), 4, 1),    # 3-D FP32 hot path: every compiled variant
+    (1, (12, 10, 128), 4, 1),   # nx = 128 and 256: the whole-row staged variants too
+    (1, (9, 10, 256), 4, 1),
     (1, (21, 19, 37), 6, 1),
     (1, (20, 16, 33), 4, 0),
     (0, (1, 45, 300), 4, 1),
