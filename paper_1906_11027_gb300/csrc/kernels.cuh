@@ -651,8 +651,10 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 // where the range wraps in y).  The periodic x shift becomes an index wrap in
 // shared memory, and the psi ring carries one wrapped column on each side.
 // NSTG stages are in flight; the interior populations wait one slab in registers.
-template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int ZC, int NSTG>
-__global__ void __launch_bounds__(NX * TY, 1)
+// PROD = 1 adds a 32-thread producer warp that only issues the copies (and takes
+// part in the block barriers), so no compute warp carries the copy issue.
+template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int ZC, int NSTG, int PROD>
+__global__ void __launch_bounds__(NX * TY + 32 * PROD, 1)
     k_onepass_row(const __grid_constant__ Pops<Real, Lattice<LAT>::Q> P, DevParams p)
 {
     using L = Lattice<LAT>;
@@ -684,7 +686,8 @@ __global__ void __launch_bounds__(NX * TY, 1)
     const int tid = threadIdx.x;
     const int tx = tid % NX, ty = tid / NX;
     const int lane = tid & 31;
-    const bool issuer = tid < 32;
+    const bool issuer = PROD ? tid >= NT : tid < 32;
+    const bool compute = !PROD || tid < NT;
 
     if (tid == 0) {
         for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
@@ -777,17 +780,18 @@ __global__ void __launch_bounds__(NX * TY, 1)
     const int last = m1 - 1 + R;
     if (issuer)
         for (; next <= last && next < base + NSTG; ++next) issue(next);
-    for (int s = m0 - R; s < m0 + R; ++s) psi_slab(s);
+    if (compute)
+        for (int s = m0 - R; s < m0 + R; ++s) psi_slab(s);
 #pragma unroll
     for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
     __syncthreads();
     if (issuer)
         for (; next <= last && next < m0 + R + NSTG; ++next) issue(next);
 
-    const bool active = (y0 + ty) < p.ny;
+    const bool active = compute && (y0 + ty) < p.ny;
     const int cell_xy = (y0 + ty) * NX + tx;
     for (int m = m0; m < m1; ++m) {
-        psi_slab(m + R);
+        if (compute) psi_slab(m + R);
         __syncthreads();
         if (issuer)
             for (; next <= last && next <= m + R + NSTG; ++next) issue(next);
@@ -1662,11 +1666,11 @@ cudaError_t launch_onepass(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int ZC, int NSTG>
+template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int ZC, int NSTG, int PROD>
 cudaError_t launch_onepass_row(const LaunchArgs& a, cudaStream_t s)
 {
     constexpr size_t dyn = sizeof(Real) * NSTG * Lattice<LAT>::Q * (TY + 2) * NX;
-    auto kern = &k_onepass_row<LAT, ORD, COLL, Real, NX, TY, ZC, NSTG>;
+    auto kern = &k_onepass_row<LAT, ORD, COLL, Real, NX, TY, ZC, NSTG, PROD>;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
@@ -1677,7 +1681,7 @@ cudaError_t launch_onepass_row(const LaunchArgs& a, cudaStream_t s)
     const int nty = (a.p.ny + TY - 1) / TY;
     const long long nblocks = static_cast<long long>(nty) * ((a.p.nz + ZC - 1) / ZC);
     const auto P = make_pops<Real, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
-    kern<<<static_cast<unsigned>(nblocks), NX * TY, dyn, s>>>(P, a.p);
+    kern<<<static_cast<unsigned>(nblocks), NX * TY + 32 * PROD, dyn, s>>>(P, a.p);
     return cudaGetLastError();
 }
 
@@ -1862,10 +1866,12 @@ KernelSet make_set()
             if constexpr (r1) {
                 add("onepass_async_64x4_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 64, 4, 16, 2>);
                 add("onepass_64x4_z16_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 16, 4, 2>);
-                add("onepass_row256x2_z32_s2", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 32, 2>, 1, 256);
-                add("onepass_row256x2_z64_s2", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 64, 2>, 1, 256);
-                add("onepass_row256x1_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 1, 32, 3>, 1, 256);
-                add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3>, 1, 128);
+                add("onepass_row256x2_z32_s2", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 32, 2, 0>, 1, 256);
+                add("onepass_row256x2_z32_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 32, 2, 1>, 1, 256);
+                add("onepass_row256x2_z24_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 24, 2, 1>, 1, 256);
+                add("onepass_row256x2_z16_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 16, 2, 1>, 1, 256);
+                add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 0>, 1, 128);
+                add("onepass_row128x4_z32_s3_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 1>, 1, 128);
                 add("onepass_x2_64x8_z16_b2_reg", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 1>, 2);
                 add("onepass_128x4_z16_b2_smem", &launch_onepass<LAT, ORD, COLL, Real, 128, 4, 16, 2, 2>);
                 add("onepass_64x4_z8_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 8, 4, 2>);
