@@ -241,6 +241,8 @@ def run_ours(args, world, rank, local):
     path = {"auto": lbm.LBM_PATH_AUTO, "two": lbm.LBM_PATH_TWO_PASS, "one": lbm.LBM_PATH_ONE_PASS}[args.path]
     dom = lbm.Domain(nx, ny, nz, lattice=wl["lattice"], stencil=wl["stencil"], G=G, tau=TAU,
                      precision=wl["precision"], stream=stream, torch_alloc=True, path=path)
+    if args.schedule:  # pin a schedule (profiling runs), else the autotuner picks
+        dom.set_schedule(args.schedule)
     dom.init_droplet(RHO_L, RHO_G, wl["R"], WIDTH)
     dom.step(args.warmup)
     torch.cuda.synchronize()
@@ -537,6 +539,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d3q19_256_fp32")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--path", choices=["auto", "two", "one"], default="auto")
+    ap.add_argument("--schedule", default=None, help="pin the step schedule by name instead of autotuning")
     ap.add_argument("--sweep", action="store_true", help="time the batched sweep instead of the step")
     ap.add_argument("--sweep-domains", type=int, default=64)
     ap.add_argument("--sweep-max-steps", type=int, default=200000)
