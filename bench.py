@@ -420,7 +420,15 @@ def run_sweep(args):
     # max|u| below FP32 velocity resolution in both arms (dissolved droplet or a
     # current too small to resolve): relative differences there are not physics
     small = [i for i in finite if max(obs32[i]["max_u"], obs64[i]["max_u"]) < args.fp64_below]
-    arms = {"batched_fp32_tanh_s": round(plain["t"], 3)}
+    # a droplet in one arm and a dissolved one (max|u| below FP32 resolution) in
+    # the other: near the critical coupling the steady state depends on the start
+    basin = [i for i in finite if i not in small and min(obs32[i]["max_u"], obs64[i]["max_u"]) < args.fp64_below]
+    # precision alone: the tanh-started FP32 batch against the same FP64 runs
+    fin_t = [i for i in range(len(doms)) if np.isfinite(obs64[i]["max_u"]) and np.isfinite(plain["obs"][i]["max_u"])]
+    ratio_t = [abs(plain["obs"][i]["max_u"] / obs64[i]["max_u"] - 1.0) for i in fin_t]
+    small_t = [i for i in fin_t if max(plain["obs"][i]["max_u"], obs64[i]["max_u"]) < args.fp64_below]
+    arms = {"batched_fp32_tanh_s": round(plain["t"], 3),
+            "diverged_tanh_fp32": sum(1 for o in plain["obs"] if not np.isfinite(o["max_u"]))}
     if warm:
         arms.update({"batched_fp32_warm_s": round(warm["t"], 3), "warm_init_s": round(warm["t_init"], 3),
                      "warm_fallbacks": warm["fallbacks"],
@@ -439,14 +447,22 @@ def run_sweep(args):
         "converged": {"batched_fp32": bool(ok32), "fp64": sum(1 for s in steps64 if s < args.sweep_max_steps)},
         "steps": {"batched_fp32_total": int(sum(steps32)), "fp64_total": int(sum(steps64))},
         "diverged": diverged,
+        "per_domain_columns": ["L", "G", "tau", "order", "R", "steps_batched", "steps_fp64", "max_u_batched",
+                               "max_u_fp64", "steps_tanh_fp32", "max_u_tanh_fp32"],
         "per_domain": [[d["nx"], round(d["G"], 3), d["tau"], d["stencil"], round(d["R"], 1), int(steps32[i]),
-                        int(steps64[i]), float("%.4g" % obs32[i]["max_u"]), float("%.4g" % obs64[i]["max_u"])]
+                        int(steps64[i]), float("%.4g" % obs32[i]["max_u"]), float("%.4g" % obs64[i]["max_u"]),
+                        int(plain["steps"][i]), float("%.4g" % plain["obs"][i]["max_u"])]
                        for i, d in enumerate(doms)] if args.sweep_details else None,
         "max_u_rel_diff": {"max": round(max(ratio), 4), "median": round(float(np.median(ratio)), 4),
                            "within_5pct": sum(1 for r in ratio if r <= 0.05), "compared": len(finite),
                            "both_below_fp64_threshold": len(small),
                            "within_5pct_or_both_below": sum(1 for i, r in zip(finite, ratio)
-                                                            if r <= 0.05 or i in small)},
+                                                            if r <= 0.05 or i in small),
+                           "droplet_in_one_arm_only": len(basin)},
+        "max_u_rel_diff_tanh_fp32_vs_fp64": {
+            "compared": len(fin_t), "within_5pct": sum(1 for r in ratio_t if r <= 0.05),
+            "within_5pct_or_both_below": sum(1 for i, r in zip(fin_t, ratio_t) if r <= 0.05 or i in small_t),
+            "median": round(float(np.median(ratio_t)), 4) if ratio_t else None},
         "arms": arms,
         "warm_start_training": train_info,
     }
@@ -462,7 +478,7 @@ def run_warmstart(args):
     from paper_1906_11027_gb300 import inputs, lbm, warmstart
 
     lbm.load()
-    doms = inputs.sweep_domains(args.sweep_domains)
+    doms = inputs.sweep_domains(args.ws_sweep_domains)
     t0 = time.perf_counter()
     b = lbm.Batch(doms, precision=lbm.LBM_FP32_SHIFTED)
     steps, obs, _ = b.run_to_steady(1e-10, args.sweep_max_steps, 100)
@@ -546,7 +562,10 @@ def main():
     ap.add_argument("--sweep-details", action="store_true")
     ap.add_argument("--sweep-warm", action="store_true",
                     help="batched arm starts from the learned warm start (network trained first on another draw)")
-    ap.add_argument("--ws-train-domains", type=int, default=128)
+    ap.add_argument("--ws-train-domains", type=int, default=256,
+                    help="domains of the separate draw the sweep's warm-start network is trained on")
+    ap.add_argument("--ws-sweep-domains", type=int, default=256,
+                    help="sweep domains whose steady states train the network of --warmstart")
     ap.add_argument("--warmstart", action="store_true", help="train and evaluate the learned warm start")
     ap.add_argument("--ws-epochs", type=int, default=80)
     ap.add_argument("--ws-heldout", type=int, default=12)

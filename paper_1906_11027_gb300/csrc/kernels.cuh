@@ -653,9 +653,11 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 // NSTG stages are in flight; the interior populations wait one slab in registers.
 // PROD = 1 adds a 32-thread producer warp that only issues the copies (and takes
 // part in the block barriers), so no compute warp carries the copy issue.
+// PROD = 2 also marks the stored populations evict-first in L2 (they are not read
+// again within the step), leaving L2 to the halo rows neighbouring tiles re-read.
 template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int ZC, int NSTG, int PROD>
-__global__ void __launch_bounds__(NX * TY + 32 * PROD, 1)
-    k_onepass_row(const __grid_constant__ Pops<Real, Lattice<LAT>::Q> P, DevParams p)
+__global__ void __launch_bounds__(NX * TY + (PROD ? 32 : 0), 1)
+    k_onepass_row(const __grid_constant__ Pops<Real, Lattice<LAT>::Q> P, DevParams p, int zc_run)
 {
     using L = Lattice<LAT>;
     using S = Stencil<3, ORD>;
@@ -680,8 +682,9 @@ __global__ void __launch_bounds__(NX * TY + 32 * PROD, 1)
     const int chunk = blockIdx.x / nty;
     const int y0 = trow * TY;
     const int nm = p.nz;
-    const int m0 = chunk * ZC;
-    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const int zc = ZC > 0 ? ZC : zc_run;  // ZC = 0: chunk length chosen at launch
+    const int m0 = chunk * zc;
+    const int m1 = (m0 + zc < nm) ? m0 + zc : nm;
     const int plane = NX * p.ny;
     const int tid = threadIdx.x;
     const int tx = tid % NX, ty = tid / NX;
@@ -802,11 +805,161 @@ __global__ void __launch_bounds__(NX * TY + 32 * PROD, 1)
             const int c = m * plane + cell_xy;
             sfor<Q>([&](auto bI) {
                 constexpr int b = decltype(bI)::value;
-                P.out[b][c] = fcur[b];
+                if (PROD == 2)
+                    __stcs(P.out[b] + c, fcur[b]);
+                else
+                    P.out[b][c] = fcur[b];
             });
         }
 #pragma unroll
         for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+    }
+    if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
+}
+
+// One-pass schedule with bulk-copy staging for 2-D lattices of reach 1 (D2Q9),
+// any force stencil up to radius 3.  A tile is TX cells of a row; the march runs
+// along y.  For row s, direction b needs row s - c_by over x0 - XP .. x0 + TX + XP
+// (XP = 16 bytes of values >= R + 1): one contiguous segment, copied by one
+// cp.async.bulk (two where it crosses the periodic x edge).  A stage stays
+// resident until the row collides, so the interior populations are read from
+// shared memory twice (psi, then collision) and nothing waits in registers;
+// stages hold NSTG rows, NSTG - R - 1 of them in flight.  A producer warp issues
+// the copies.
+template <int LAT, int ORD, int COLL, class Real, int TX, int ZC, int NSTG>
+__global__ void __launch_bounds__(TX + 32, 1)
+    k_onepass_seg(const __grid_constant__ Pops<Real, Lattice<LAT>::Q> P, DevParams p, int ntx)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<2, ORD>;
+    constexpr int R = S::radius;
+    constexpr int Q = L::Q;
+    static_assert(L::D == 2 && L::reach == 1, "segment staging is written for 2-D reach-1 lattices");
+    constexpr int XP = 16 / static_cast<int>(sizeof(Real));
+    static_assert(XP >= R + 1 && TX % XP == 0 && TX % 32 == 0, "x pad / tile");
+    constexpr int W = TX + 2 * XP;   // staged segment length
+    constexpr int EX = TX + 2 * R;   // psi ring row
+    constexpr int NS = 2 * R + 2;
+    constexpr int STG = Q * W;
+    static_assert(NSTG >= R + 2 && NSTG >= 2 * R, "one row in flight; the 2R warm-up rows staged at once");
+    __shared__ Real ring[NS * EX];
+    __shared__ alignas(8) unsigned long long bars[NSTG];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    Real* stage = reinterpret_cast<Real*>(dyn_smem);  // [NSTG][Q][W]
+
+    const int tile = blockIdx.x % ntx;
+    const int chunk = blockIdx.x / ntx;
+    const int x0 = tile * TX;
+    const int nm = p.ny;
+    const int m0 = chunk * ZC;
+    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const bool producer = tid >= TX;
+
+    if (tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    int cby = 0;
+    const Real* src_b = nullptr;
+    sfor<Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int vy = L::T.v[b][1];
+        if (lane == b) {
+            cby = vy;
+            src_b = P.in[b];
+        }
+    });
+    const int base = m0 - R;
+    auto issue = [&](int s) {
+        const int slot = (s - base) % NSTG;
+        const uint32_t bar = smem_u32(&bars[slot]);
+        if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(STG * sizeof(Real)));
+        __syncwarp();
+        if (lane < Q) {
+            fence_proxy_async_smem();
+            const Real* row = src_b + static_cast<long long>(wrap_any(s - cby, nm)) * p.nx;
+            uint32_t dst = smem_u32(stage + slot * STG + lane * W);
+            int xs = x0 - XP, left = W;
+            while (left > 0) {
+                const int x = wrap_any(xs, p.nx);
+                const int n = (p.nx - x < left) ? p.nx - x : left;
+                bulk_g2s(dst, row + x, static_cast<uint32_t>(n * sizeof(Real)), bar);
+                dst += static_cast<uint32_t>(n * sizeof(Real));
+                xs += n;
+                left -= n;
+            }
+        }
+    };
+    uint32_t phase = 0;
+    bool ok = true;
+    auto stage_of = [&](int s) { return stage + ((s - base) % NSTG) * STG; };
+    auto wait_stage = [&](int s) {
+        const int slot = (s - base) % NSTG;
+        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        phase ^= 1u << slot;
+    };
+    // f of the cell at tile offset cx (-R .. TX + R - 1) from stage st (pull)
+    auto load_cell = [&](const Real* st, int cx, Real (&f)[Q]) {
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int vx = L::T.v[b][0];
+            f[b] = st[b * W + cx + XP - vx];
+        });
+    };
+    auto rho_psi = [&](const Real (&f)[Q]) {
+        Real sum = Real(0);
+        sfor<Q>([&](auto bI) { sum += f[decltype(bI)::value]; });
+        const Real rho = std::is_same<Real, float>::value ? Real(p.rho_bar) + sum : sum;
+        return psi_of<LAT>(rho, p);
+    };
+    auto psi_slab = [&](int s) {
+        wait_stage(s);
+        const Real* st = stage_of(s);
+        Real* dst = ring + ring_slot(s, NS) * EX;
+        Real f[Q];
+        load_cell(st, tid, f);
+        dst[tid + R] = rho_psi(f);
+        if (tid < 2 * R) {
+            const int cx = (tid < R) ? tid - R : TX + tid - R;
+            load_cell(st, cx, f);
+            dst[cx + R] = rho_psi(f);
+        }
+    };
+
+    int next = base;
+    const int last = m1 - 1 + R;
+    if (producer)
+        for (; next <= last && next < base + NSTG; ++next) issue(next);
+    if (!producer)
+        for (int s = m0 - R; s < m0 + R; ++s) psi_slab(s);
+    __syncthreads();
+    // slabs below m0 are consumed (psi only): slab k may refill slab k - NSTG's stage
+    if (producer)
+        for (; next <= last && next < m0 + NSTG; ++next) issue(next);
+
+    const bool active = !producer && (x0 + tid) < p.nx;
+    for (int m = m0; m < m1; ++m) {
+        if (!producer) psi_slab(m + R);
+        __syncthreads();
+        // every thread is past the collision of row m - 1
+        if (producer)
+            for (; next <= last && next <= m - 1 + NSTG; ++next) issue(next);
+        if (active) {
+            Real f[Q];
+            load_cell(stage_of(m), tid, f);
+            Real F[3];
+            force_ring<LAT, ORD, Real, EX, EX, NS>(ring, m, tid + R, 0, p.G, F);
+            collide<LAT, COLL>(f, F, p);
+            const int c = m * p.nx + x0 + tid;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                __stcs(P.out[b] + c, f[b]);
+            });
+        }
     }
     if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
 }
@@ -1679,9 +1832,48 @@ cudaError_t launch_onepass_row(const LaunchArgs& a, cudaStream_t s)
     }
     if (a.p.nx != NX) return cudaErrorInvalidValue;
     const int nty = (a.p.ny + TY - 1) / TY;
-    const long long nblocks = static_cast<long long>(nty) * ((a.p.nz + ZC - 1) / ZC);
+    int zc = ZC;
+    if (ZC == 0) {
+        // one block per SM (shared memory): pick the chunk count that minimises
+        // waves x (slabs per chunk + the two warm-up slabs of every chunk)
+        int dev = 0, nsm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        long long best = -1;
+        for (int nc = 1; nc <= a.p.nz; ++nc) {
+            const int len = (a.p.nz + nc - 1) / nc;
+            const int used = (a.p.nz + len - 1) / len;  // chunks actually launched
+            const long long waves = (static_cast<long long>(nty) * used + nsm - 1) / nsm;
+            const long long cost = waves * (len + 2);
+            if (best < 0 || cost < best) {
+                best = cost;
+                zc = len;
+            }
+        }
+    }
+    const long long nblocks = static_cast<long long>(nty) * ((a.p.nz + zc - 1) / zc);
     const auto P = make_pops<Real, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
-    kern<<<static_cast<unsigned>(nblocks), NX * TY + 32 * PROD, dyn, s>>>(P, a.p);
+    kern<<<static_cast<unsigned>(nblocks), NX * TY + (PROD ? 32 : 0), dyn, s>>>(P, a.p, zc);
+    return cudaGetLastError();
+}
+
+template <int LAT, int ORD, int COLL, class Real, int TX, int ZC, int NSTG>
+cudaError_t launch_onepass_seg(const LaunchArgs& a, cudaStream_t s)
+{
+    constexpr int XP = 16 / static_cast<int>(sizeof(Real));
+    constexpr size_t dyn = sizeof(Real) * NSTG * Lattice<LAT>::Q * (TX + 2 * XP);
+    auto kern = &k_onepass_seg<LAT, ORD, COLL, Real, TX, ZC, NSTG>;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.p.nx % XP != 0) return cudaErrorInvalidValue;
+    const int ntx = (a.p.nx + TX - 1) / TX;
+    const long long nblocks = static_cast<long long>(ntx) * ((a.p.ny + ZC - 1) / ZC);
+    const auto P = make_pops<Real, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
+    kern<<<static_cast<unsigned>(nblocks), TX + 32, dyn, s>>>(P, a.p, ntx);
     return cudaGetLastError();
 }
 
@@ -1868,10 +2060,11 @@ KernelSet make_set()
                 add("onepass_64x4_z16_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 16, 4, 2>);
                 add("onepass_row256x2_z32_s2", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 32, 2, 0>, 1, 256);
                 add("onepass_row256x2_z32_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 32, 2, 1>, 1, 256);
-                add("onepass_row256x2_z24_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 24, 2, 1>, 1, 256);
-                add("onepass_row256x2_z16_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 16, 2, 1>, 1, 256);
+                add("onepass_row256x2_zauto_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 0, 2, 1>, 1, 256);
+                add("onepass_row256x2_zauto_s2_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 0, 2, 2>, 1, 256);
                 add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 0>, 1, 128);
                 add("onepass_row128x4_z32_s3_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 1>, 1, 128);
+                add("onepass_row128x4_zauto_s3_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 0, 3, 2>, 1, 128);
                 add("onepass_x2_64x8_z16_b2_reg", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 1>, 2);
                 add("onepass_128x4_z16_b2_smem", &launch_onepass<LAT, ORD, COLL, Real, 128, 4, 16, 2, 2>);
                 add("onepass_64x4_z8_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 64, 4, 8, 4, 2>);
@@ -1894,6 +2087,12 @@ KernelSet make_set()
             if constexpr (r1) add("onepass_256_z16_b3_reg", &launch_onepass<LAT, ORD, COLL, Real, 256, 1, 16, 3, 1>);
             add("onepass_async_256_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 256, 1, 16, 2>);
             add("onepass_x2_256_z16_b2_smem", &launch_onepass_x2<LAT, ORD, 128, 1, 16, 2, 2>, 2);
+            if constexpr (Lattice<LAT>::reach == 1) {
+                add("onepass_seg256_z64_s8", &launch_onepass_seg<LAT, ORD, COLL, Real, 256, 64, 8>, 4);
+                add("onepass_seg256_z64_s6", &launch_onepass_seg<LAT, ORD, COLL, Real, 256, 64, 6>, 4);
+                add("onepass_seg128_z64_s8", &launch_onepass_seg<LAT, ORD, COLL, Real, 128, 64, 8>, 4);
+                add("onepass_seg512_z64_s6", &launch_onepass_seg<LAT, ORD, COLL, Real, 512, 64, 6>, 4);
+            }
         }
     }
     k.obs = &launch_obs<LAT, ORD, Real>;

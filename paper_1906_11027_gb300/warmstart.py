@@ -15,6 +15,8 @@ import numpy as np
 from . import lbm
 
 DMAX = 12.0
+MAX_G = -4.5        # the library keeps the tanh start above this coupling
+MIN_CONTRAST = 0.2  # rho_l - rho_g of a steady droplet (a dissolved one is not a sample)
 
 
 def steady_samples(rho, G, tau, order, max_per_domain=4096, rng=None):
@@ -22,7 +24,7 @@ def steady_samples(rho, G, tau, order, max_per_domain=4096, rng=None):
     ny, nx = rho.shape
     rl = float(rho[ny // 2, nx // 2])
     rg = float(rho[0, 0])
-    if not (np.isfinite(rl) and np.isfinite(rg)) or rl - rg < 1e-3:
+    if not (np.isfinite(rl) and np.isfinite(rg)) or rl - rg < MIN_CONTRAST:
         return None
     Rs = float(np.sqrt(max((rho - rg).sum() / (rl - rg), 0.0) / np.pi))
     yy, xx = np.meshgrid(np.arange(ny) - ny // 2, np.arange(nx) - nx // 2, indexing="ij")
@@ -42,7 +44,7 @@ def steady_samples(rho, G, tau, order, max_per_domain=4096, rng=None):
 def dataset_from_batch(batch, domains, obs, seed=11027, holdout=0.1, max_per_domain=4096):
     """(X_train, y_train, X_val, y_val, held-out domain indices) from a converged batch."""
     rng = np.random.default_rng(seed)
-    good = [i for i, o in enumerate(obs) if np.isfinite(o["max_u"])]
+    good = [i for i, o in enumerate(obs) if np.isfinite(o["max_u"]) and domains[i]["G"] <= MAX_G]
     held = set(rng.choice(good, size=max(1, int(round(holdout * len(good)))), replace=False).tolist())
     parts = {True: ([], []), False: ([], [])}
     for i in good:

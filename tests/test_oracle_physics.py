@@ -22,6 +22,7 @@ from scipy.integrate import quad
 from scipy.optimize import brentq, fsolve
 
 import oracle
+from theory import mechanical_stability
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -134,20 +135,6 @@ def test_peng_robinson_density_ratio_range():
     assert 0.8 * hi_ratio < rl / rv < 1.25 * hi_ratio
     ratios = [np.divide(*maxwell(t)[::-1]) for t in (0.6, 0.7, 0.8, 0.9, 0.95)]
     assert all(np.diff(ratios) < 0)
-
-
-def mechanical_stability(G, eps, cs2=1 / 3):
-    psi = lambda r: -np.expm1(-r)
-    dpsi = lambda r: np.exp(-r)
-    p = lambda r: cs2 * r + 0.5 * G * cs2 * psi(r) ** 2
-
-    def eqs(v):
-        rg, rl = v
-        p0 = p(rl)
-        integral = quad(lambda r: (p0 - p(r)) * dpsi(r) / psi(r) ** (1 + eps), rg, rl,
-                        epsabs=1e-14, epsrel=1e-13, limit=200)[0]
-        return [p(rg) - p(rl), integral]
-    return fsolve(eqs, [0.12, 1.9], xtol=1e-13)
 
 
 @pytest.mark.parametrize("G,tol_g", [(-5.0, 3e-3), (-5.5, 2e-2)])
