@@ -160,6 +160,157 @@ __global__ void __launch_bounds__(TX) k_batch_step(const BatchDom* __restrict__ 
     }
 }
 
+// Segment-staged work item (FP32; nx a multiple of 4): the bulk-copy pipeline of
+// the single-domain 2-D kernel.  A producer warp (threads TX .. TX + 31) copies,
+// per row s and direction b, the contiguous segment of row s - c_by over
+// x0 - 4 .. x0 + TX + 4 into a stage (two copies where it crosses the periodic x
+// edge); the stage stays resident until the row collides.  mbarrier phases run
+// on across the items a block processes.
+template <int ORD, int TX, int ZC, int NSTG>
+__device__ __forceinline__ void batch_item_seg(const float* __restrict__ A, float* __restrict__ Bo, const DevParams& p, int x0,
+                               int m0, float* ring, float* stage, unsigned long long* bars, uint32_t& phase, bool& ok)
+{
+    using L = Lattice<kLatD2Q9>;
+    constexpr int R = Stencil<2, ORD>::radius;
+    constexpr int Q = kQ9;
+    constexpr int XP = 4;
+    constexpr int W = TX + 2 * XP;
+    constexpr int EX = TX + 2 * R;
+    constexpr int NS = 2 * R + 2;
+    constexpr int STG = Q * W;
+    static_assert(NSTG >= R + 2 && NSTG >= 2 * R && XP >= R + 1, "stages / pad");
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const bool producer = tid >= TX;
+    const int nm = p.ny;
+    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const long long N = static_cast<long long>(p.nx) * p.ny;
+    int cby = 0;
+    sfor<Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int vy = L::T.v[b][1];
+        if (lane == b) cby = vy;
+    });
+    const float* src_b = A + static_cast<long long>(lane < Q ? lane : 0) * N;
+    const int base = m0 - R;
+    auto issue = [&](int s) {
+        const int slot = (s - base) % NSTG;
+        const uint32_t bar = smem_u32(&bars[slot]);
+        if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(STG * sizeof(float)));
+        __syncwarp();
+        if (lane < Q) {
+            fence_proxy_async_smem();
+            const float* row = src_b + static_cast<long long>(wrap_any(s - cby, nm)) * p.nx;
+            uint32_t dst = smem_u32(stage + slot * STG + lane * W);
+            int xs = x0 - XP, left = W;
+            while (left > 0) {
+                const int x = wrap_any(xs, p.nx);
+                const int n = (p.nx - x < left) ? p.nx - x : left;
+                bulk_g2s(dst, row + x, static_cast<uint32_t>(n * sizeof(float)), bar);
+                dst += static_cast<uint32_t>(n * sizeof(float));
+                xs += n;
+                left -= n;
+            }
+        }
+    };
+    auto stage_of = [&](int s) { return stage + ((s - base) % NSTG) * STG; };
+    auto wait_stage = [&](int s) {
+        const int slot = (s - base) % NSTG;
+        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        phase ^= 1u << slot;
+    };
+    auto load_cell = [&](const float* st, int cx, float (&f)[Q]) {
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int vx = L::T.v[b][0];
+            f[b] = st[b * W + cx + XP - vx];
+        });
+    };
+    auto rho_psi = [&](const float (&f)[Q]) {
+        float sum = 0.f;
+        sfor<Q>([&](auto bI) { sum += f[decltype(bI)::value]; });
+        return psi_of<kLatD2Q9>(static_cast<float>(p.rho_bar) + sum, p);
+    };
+    auto psi_slab = [&](int s) {
+        wait_stage(s);
+        const float* st = stage_of(s);
+        float* dst = ring + ring_slot(s, NS) * EX;
+        float f[Q];
+        load_cell(st, tid, f);
+        dst[tid + R] = rho_psi(f);
+        if (tid < 2 * R) {
+            const int cx = (tid < R) ? tid - R : TX + tid - R;
+            load_cell(st, cx, f);
+            dst[cx + R] = rho_psi(f);
+        }
+    };
+    int next = base;
+    const int last = m1 - 1 + R;
+    if (producer)
+        for (; next <= last && next < base + NSTG; ++next) issue(next);
+    if (!producer)
+        for (int s = m0 - R; s < m0 + R; ++s) psi_slab(s);
+    __syncthreads();
+    if (producer)
+        for (; next <= last && next < m0 + NSTG; ++next) issue(next);
+    const bool active = !producer && (x0 + tid) < p.nx;
+    for (int m = m0; m < m1; ++m) {
+        if (!producer) psi_slab(m + R);
+        __syncthreads();
+        if (producer)
+            for (; next <= last && next <= m - 1 + NSTG; ++next) issue(next);
+        if (active) {
+            float f[Q];
+            load_cell(stage_of(m), tid, f);
+            float F[3];
+            force_ring<kLatD2Q9, ORD, float, EX, EX, NS>(ring, m, tid + R, 0, p.G, F);
+            collide<kLatD2Q9, 0>(f, F, p);
+            const long long c = static_cast<long long>(m) * p.nx + x0 + tid;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                __stcs(Bo + b * N + c, f[b]);
+            });
+        }
+    }
+}
+
+template <int TX, int ZC, int NSTG>
+__global__ void __launch_bounds__(TX + 32) k_batch_step_seg(const BatchDom* __restrict__ doms,
+                                                            const int4* __restrict__ items,
+                                                            const int* __restrict__ nitems,
+                                                            const float* __restrict__ pool_in,
+                                                            float* __restrict__ pool_out, unsigned* __restrict__ err)
+{
+    __shared__ float ring[kBNS * (TX + 2 * kBMaxR)];
+    __shared__ alignas(8) unsigned long long bars[NSTG];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    float* stage = reinterpret_cast<float*>(dyn_smem);  // [NSTG][9][TX + 8]
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    bool ok = true;
+    const int n = *nitems;
+    for (int it = blockIdx.x; it < n; it += gridDim.x) {
+        const int4 w = items[it];
+        const BatchDom d = doms[w.x];
+        const DevParams p = dom_params(d);
+        const float* A = pool_in + d.off;
+        float* Bo = pool_out + d.off;
+        const int x0 = w.y * TX, m0 = w.z * ZC;
+        switch (d.order) {
+        case 4: batch_item_seg<4, TX, ZC, NSTG>(A, Bo, p, x0, m0, ring, stage, bars, phase, ok); break;
+        case 6: batch_item_seg<6, TX, ZC, NSTG>(A, Bo, p, x0, m0, ring, stage, bars, phase, ok); break;
+        case 8: batch_item_seg<8, TX, ZC, NSTG>(A, Bo, p, x0, m0, ring, stage, bars, phase, ok); break;
+        default: batch_item_seg<10, TX, ZC, NSTG>(A, Bo, p, x0, m0, ring, stage, bars, phase, ok); break;
+        }
+        __syncthreads();  // stages and ring are reused by the next item
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(err, kErrTimeout);
+}
+
 // Per-cell macroscopic values of domain d at cell i (pulled populations, psi of
 // the neighbourhood recomputed from the populations; used by the observables).
 template <int ORD, class Real>
@@ -362,6 +513,8 @@ struct lbm_batch {
     cudaGraphExec_t graph[2];
     int graph_k;
     int graph_cur;  // parity the graph was captured from
+    unsigned* d_err;  // device error word (a bounded wait that ran out)
+    unsigned* h_err;  // pinned copy, read after every graph block
     int var;        // tile shape in use (index into the variant table)
     bool tuned;     // autotuner has run, or a shape was pinned
     std::vector<double> tune_ms;  // ms per step of each shape (< 0: not timed)
@@ -395,6 +548,7 @@ struct BatchVariant {
     int tx, zc;
     cudaError_t (*launch)(lbm_batch* b, int parity);
     int (*occupancy)(int fp32);
+    bool staged;  // bulk-copy staging: FP32 only, every nx a multiple of 4
 };
 
 template <int TX, int ZC>
@@ -422,14 +576,45 @@ int occupancy_variant(int fp32)
     return occ;
 }
 
+template <int TX, int ZC, int NSTG>
+constexpr size_t seg_dyn_bytes()
+{
+    return sizeof(float) * NSTG * kQ9 * (TX + 8);
+}
+
+template <int TX, int ZC, int NSTG>
+cudaError_t launch_seg(lbm_batch* b, int parity)
+{
+    auto kern = &k_batch_step_seg<TX, ZC, NSTG>;
+    kern<<<b->grid, TX + 32, seg_dyn_bytes<TX, ZC, NSTG>(), b->stream>>>(
+        b->d_doms, b->d_items, b->d_nitems, static_cast<const float*>(b->pool[parity]),
+        static_cast<float*>(b->pool[parity ^ 1]), b->d_err);
+    return cudaGetLastError();
+}
+
+template <int TX, int ZC, int NSTG>
+int occupancy_seg(int)
+{
+    auto kern = &k_batch_step_seg<TX, ZC, NSTG>;
+    constexpr size_t dyn = seg_dyn_bytes<TX, ZC, NSTG>();
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX + 32, dyn);
+    return occ;
+}
+
 const BatchVariant kBatchVariants[] = {
-    {"tile64_rows16", 64, 16, &launch_variant<64, 16>, &occupancy_variant<64, 16>},
-    {"tile32_rows16", 32, 16, &launch_variant<32, 16>, &occupancy_variant<32, 16>},
-    {"tile32_rows32", 32, 32, &launch_variant<32, 32>, &occupancy_variant<32, 32>},
-    {"tile64_rows8", 64, 8, &launch_variant<64, 8>, &occupancy_variant<64, 8>},
-    {"tile64_rows32", 64, 32, &launch_variant<64, 32>, &occupancy_variant<64, 32>},
-    {"tile128_rows16", 128, 16, &launch_variant<128, 16>, &occupancy_variant<128, 16>},
-    {"tile128_rows32", 128, 32, &launch_variant<128, 32>, &occupancy_variant<128, 32>},
+    {"tile64_rows16", 64, 16, &launch_variant<64, 16>, &occupancy_variant<64, 16>, false},
+    {"tile32_rows16", 32, 16, &launch_variant<32, 16>, &occupancy_variant<32, 16>, false},
+    {"tile32_rows32", 32, 32, &launch_variant<32, 32>, &occupancy_variant<32, 32>, false},
+    {"tile64_rows8", 64, 8, &launch_variant<64, 8>, &occupancy_variant<64, 8>, false},
+    {"tile64_rows32", 64, 32, &launch_variant<64, 32>, &occupancy_variant<64, 32>, false},
+    {"tile128_rows16", 128, 16, &launch_variant<128, 16>, &occupancy_variant<128, 16>, false},
+    {"tile128_rows32", 128, 32, &launch_variant<128, 32>, &occupancy_variant<128, 32>, false},
+    {"staged64_rows32", 64, 32, &launch_seg<64, 32, 8>, &occupancy_seg<64, 32, 8>, true},
+    {"staged128_rows32", 128, 32, &launch_seg<128, 32, 8>, &occupancy_seg<128, 32, 8>, true},
+    {"staged128_rows64", 128, 64, &launch_seg<128, 64, 8>, &occupancy_seg<128, 64, 8>, true},
+    {"staged256_rows64", 256, 64, &launch_seg<256, 64, 8>, &occupancy_seg<256, 64, 8>, true},
 };
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 constexpr int kMinTX = 32, kMinZC = 8;  // smallest tile and chunk of the table (item buffer size)
@@ -506,8 +691,11 @@ int autotune(lbm_batch* b)
     ck(cudaMemcpyAsync(save, b->pool[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
     constexpr int kWarm = 2, kTimed = 8;
     b->tune_ms.assign(kNumBatchVariants, -1.0);
+    bool nx4 = true;
+    for (const auto& m : b->doms) nx4 = nx4 && m.nx % 4 == 0;
     int best = 0;
     for (int v = 0; v < kNumBatchVariants && rc == LBM_OK; ++v) {
+        if (kBatchVariants[v].staged && !(b->fp32 && nx4)) continue;
         if (int r = select_variant(b, v)) {
             rc = r;
             break;
@@ -646,12 +834,14 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
     b->d_res = static_cast<double*>(b->dalloc(sizeof(double) * n * 8));
     b->d_prev = static_cast<double*>(b->dalloc(sizeof(double) * n));
     b->d_newly = static_cast<int*>(b->dalloc(256));
+    b->d_err = static_cast<unsigned*>(b->dalloc(256));
     if (!b->pool[0] || !b->pool[1] || !b->d_doms || !b->d_items || !b->d_nitems || !b->d_cur_of || !b->d_init ||
-        !b->d_partials || !b->d_res || !b->d_prev || !b->d_newly) {
+        !b->d_partials || !b->d_res || !b->d_prev || !b->d_newly || !b->d_err) {
         lbm_batch_destroy(b);
         return set_last_error(LBM_ENOMEM, "lbm_batch_create: device allocation failed");
     }
-    if (cudaMallocHost(&b->h_newly, sizeof(int)) != cudaSuccess) {
+    if (cudaMallocHost(&b->h_newly, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&b->h_err, sizeof(unsigned)) != cudaSuccess) {
         lbm_batch_destroy(b);
         return set_last_error(LBM_ENOMEM, "pinned host allocation failed");
     }
@@ -662,6 +852,7 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
     ck(cudaMemcpyAsync(b->d_doms, b->doms.data(), sizeof(BatchDom) * n, cudaMemcpyHostToDevice, b->stream));
     ck(cudaMemcpyAsync(b->d_init, init, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, b->stream));
     ck(cudaMemsetAsync(b->d_cur_of, 0, sizeof(int) * n, b->stream));
+    ck(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream));
     std::vector<double> prev(n, -1.0);
     ck(cudaMemcpyAsync(b->d_prev, prev.data(), sizeof(double) * n, cudaMemcpyHostToDevice, b->stream));
     ck(cudaMemsetAsync(b->pool[1], 0, es * off, b->stream));
@@ -700,7 +891,9 @@ int lbm_batch_destroy(lbm_batch* b)
     b->dfree(b->d_res);
     b->dfree(b->d_prev);
     b->dfree(b->d_newly);
+    b->dfree(b->d_err);
     if (b->h_newly) cudaFreeHost(b->h_newly);
+    if (b->h_err) cudaFreeHost(b->h_err);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return LBM_OK;
@@ -753,6 +946,7 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_newly, b->d_newly, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -779,6 +973,7 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t
     while (nactive > 0 && taken + K <= max_steps) {
         LBM_BCK(cudaGraphLaunch(b->graph[0], b->stream));
         LBM_BCK(cudaStreamSynchronize(b->stream));
+        if (*b->h_err & kErrTimeout) return set_last_error(LBM_ETIMEOUT, "a bounded device wait ran out");
         taken += K;
         b->global_step += K;
         for (int d = 0; d < b->n; ++d)
@@ -837,8 +1032,12 @@ int lbm_batch_set_schedule(lbm_batch* b, const char* name)
 {
     if (!b || !name) return set_last_error(LBM_EINVAL, "lbm_batch_set_schedule: bad argument");
     LBM_BCK(cudaSetDevice(b->device));
+    bool nx4 = true;
+    for (const auto& m : b->doms) nx4 = nx4 && m.nx % 4 == 0;
     for (int v = 0; v < kNumBatchVariants; ++v)
         if (std::strcmp(kBatchVariants[v].name, name) == 0) {
+            if (kBatchVariants[v].staged && !(b->fp32 && nx4))
+                return set_last_error(LBM_EINVAL, "lbm_batch_set_schedule: staged shapes need FP32 and nx % 4 == 0");
             b->tuned = true;
             return select_variant(b, v);
         }

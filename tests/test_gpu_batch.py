@@ -140,3 +140,39 @@ def test_batch_autotuner_reports_and_every_shape_is_bitwise_equal(lbm):
     with pytest.raises(lbm.LbmError):
         b.set_schedule("no_such_shape")
     b.close()
+
+
+STAGED_DOMAINS = [
+    dict(nx=64, ny=64, G=-5.0, tau=1.0, stencil=4, rho_l=2.0, rho_g=0.15, R=16.0, width=2.0),
+    dict(nx=96, ny=80, G=-4.8, tau=0.8, stencil=6, rho_l=1.8, rho_g=0.2, R=20.0, width=2.0),
+    dict(nx=68, ny=45, G=-5.5, tau=0.6, stencil=10, rho_l=2.2, rho_g=0.1, R=9.0, width=2.0),
+    dict(nx=132, ny=70, G=-5.2, tau=1.0, stencil=8, rho_l=2.0, rho_g=0.13, R=14.0, width=3.0),
+]
+
+
+def test_batch_staged_shapes_match_oracle_and_each_other(lbm):
+    """Bulk-copy staged shapes (FP32, every nx a multiple of 4; ragged tiles and
+    row chunks): each matches the oracle per domain and the plain tiled shape
+    bit for bit; an FP64 batch refuses them."""
+    b = lbm.Batch(STAGED_DOMAINS, precision=1)
+    names = [k for k in b.schedule_report() if k != "chosen"]
+    b.close()
+    staged = [n for n in names if n.startswith("staged")]
+    assert len(staged) >= 3
+    outs = {}
+    for name in ["tile64_rows16"] + staged:
+        b = lbm.Batch(STAGED_DOMAINS, precision=1)
+        b.set_schedule(name)
+        b.step(41)
+        outs[name] = [b.get_f(i) for i in range(len(STAGED_DOMAINS))]
+        b.close()
+    for name in staged:
+        for a, c in zip(outs[name], outs["tile64_rows16"]):
+            assert np.array_equal(a, c), name
+    for i, d in enumerate(STAGED_DOMAINS):
+        ref = oracle_run(d, 41).get_f()
+        assert np.abs(outs[staged[0]][i] - ref).max() <= 1e-5 * np.abs(ref).max(), i
+    b = lbm.Batch(STAGED_DOMAINS, precision=0)
+    with pytest.raises(lbm.LbmError):
+        b.set_schedule(staged[0])
+    b.close()
