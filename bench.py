@@ -40,12 +40,18 @@ WORKLOADS = {
     "d2q9_8192_fp32": dict(lattice=0, shape=(1, 8192, 8192), precision=1, stencil=4, R=2048.0,
                            desc="D2Q9 BGK FP32-shifted 8192^2 periodic, psi=1-exp(-rho), G=-5, 4th-order stencil, "
                                 "centred droplet R=2048"),
+    "d2q9_2048_fp64": dict(lattice=0, shape=(1, 2048, 2048), precision=0, stencil=4, R=512.0, alu=True,
+                           desc="D2Q9 BGK FP64 2048^2 periodic, psi=1-exp(-rho), G=-5, 4th-order stencil, "
+                                "centred droplet R=512 (FP64-ALU-bound on GB300)"),
     "d2q9_64_fp64": dict(lattice=0, shape=(1, 64, 64), precision=0, stencil=4, R=16.0,
                          desc="D2Q9 BGK FP64 64^2 periodic, psi=1-exp(-rho), G=-5, 4th-order stencil, "
                               "centred droplet R=16"),
 }
 RHO_L, RHO_G, WIDTH, G, TAU = 2.0, 0.15, 2.0, -5.0, 1.0
 HBM_FALLBACK_GBS = 6800.0
+# No FP64 peak is measured on this machine; the nominal GB300 FP64 rate (non-tensor)
+# is the ALU roofline of the FP64 step.
+FP64_NOMINAL_GFLOPS = 1250.0
 
 
 def measured_peak_gbs():
@@ -79,6 +85,20 @@ def recorded_traffic(kernel, workload):
         if e.get("source_hash") != kernel_source_hash():
             return None
         return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def recorded_flops(kernel, workload):
+    """FP64 flops per cell from the committed ncu instruction counts, if they were
+    taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "fp64_flops.json")
+    try:
+        with open(path) as fh:
+            e = json.load(fh)[workload][kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["flops_per_cell"])
     except Exception:
         return None
 
@@ -177,9 +197,11 @@ def job_mlups(world, cells_per_rank, steps, max_elapsed_ms):
     return world * cells_per_rank * steps / (max_elapsed_ms * 1e-3) / 1e6
 
 
-def oracle_sample_run(wl, budget_s, steps):
+def oracle_sample_run(wl, budget_s, steps, fill_budget=False):
     """Time the FP64 oracle for `steps` steps on a box of the workload's lattice,
-    stencil and droplet, its side chosen so the run takes about budget_s.
+    stencil and droplet, its side chosen so the run takes about budget_s (capped
+    at the workload's own side; with fill_budget the step count then grows to
+    fill the budget).
 
     Returns (MLUPS, sample description, cores, seconds)."""
     import oracle
@@ -195,6 +217,8 @@ def oracle_sample_run(wl, budget_s, steps):
     del probe
     L = int((budget_s * rate / steps) ** (1.0 / dim))
     L = max(16, min(nx, (L // 8) * 8))
+    if fill_budget:
+        steps = max(steps, int(budget_s * rate / L ** dim))
     sim = oracle.Sim(lat, L, L, L if dim == 3 else 1, stencil=wl["stencil"], G=G, tau=TAU)
     sim.init_droplet(RHO_L, RHO_G, wl["R"] * L / nx, WIDTH)
     t0 = time.perf_counter()
@@ -322,8 +346,19 @@ def run_ours(args, world, rank, local):
                 "note": f"init_from_rho(host) + step({e2e_steps}) + observables(); mass {obs['mass']:.6e}"},
     }
     dom.close()
+    if wl.get("alu"):
+        # FP64 on GB300: the step is bound by FP64 arithmetic, not by HBM
+        fpc = recorded_flops(dom_k, args.workload)
+        gflops = fpc * cells / (kernel_ms[dom_k] * 1e-3) / 1e9 if fpc else None
+        line["roofline"] = {
+            "bound": "alu", "kernel": dom_k, "achieved": round(gflops, 1) if gflops else None,
+            "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+            "frac": round(gflops / FP64_NOMINAL_GFLOPS, 4) if gflops else None, "traffic": traffic,
+            "flops_per_cell": fpc, "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+            "hbm_context": {"achieved_gbs": round(achieved, 1), "frac_of_measured_copy": round(achieved / peak, 4)},
+            "kernel_ms": {k: round(v, 5) for k, v in kernel_ms.items()}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mlups, sample, cores, _ = oracle_sample_run(wl, args.cpu_budget, 4)
+        mlups, sample, cores, _ = oracle_sample_run(wl, args.cpu_budget, 4, fill_budget=True)
         line["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                                 "sample": sample}
     if rank == 0:

@@ -242,15 +242,18 @@ int lbm_batch_get_populations(lbm_batch* b, int d, double* f_host);
 int lbm_batch_set_populations(lbm_batch* b, int d, const double* f_host);
 
 /* Tile shape of the batch step kernel (cells per tile along x by rows per work
- * item).  The first lbm_batch_step / lbm_batch_run_to_steady (or this call) times
- * every compiled shape for a few steps on the batch's current state, restores the
- * state, and keeps the fastest; all shapes perform the same per-cell arithmetic,
- * so results are bitwise the same whichever is chosen.  The report is
- * "chosen=NAME;NAME=ms;..." in buf (NUL-terminated, truncated to len). */
+ * item): "tileTX_rowsZC" shapes gather populations per thread; "stagedTX_rowsZC"
+ * shapes stage each row segment in shared memory with bulk copies (FP32 batches
+ * whose every nx is a multiple of 4 only).  The first lbm_batch_step /
+ * lbm_batch_run_to_steady (or this call) times every applicable shape for a few
+ * steps on the batch's current state, restores the state, and keeps the
+ * fastest; all shapes perform the same per-cell arithmetic, so results are
+ * bitwise the same whichever is chosen.  The report is "chosen=NAME;NAME=ms;..."
+ * in buf (NUL-terminated, truncated to len). */
 int lbm_batch_schedule_report(lbm_batch* b, char* buf, int len);
 
-/* Pins the tile shape to the named one (a name the report lists), skipping the
- * autotuner; LBM_EINVAL for an unknown name. */
+/* Pins the tile shape to the named one, skipping the autotuner; LBM_EINVAL for
+ * an unknown name or a staged shape the batch does not qualify for. */
 int lbm_batch_set_schedule(lbm_batch* b, const char* name);
 
 /* ---- learned warm start ------------------------------------------------------ */
