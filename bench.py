@@ -407,6 +407,8 @@ def run_sweep(args):
         fallbacks = warmstart.batch_warm_init(b, doms, net) if warm else None
         t_init = time.perf_counter() - t0
         steps32, obs32, ok32 = b.run_to_steady(1e-10, args.sweep_max_steps, K)
+        torch.cuda.synchronize()
+        t_fp32 = time.perf_counter() - t0
         # precision policy: a steady current below FP32's velocity resolution is
         # re-converged in FP64, continued from the FP32 state
         tiny = [i for i, o in enumerate(obs32) if np.isfinite(o["max_u"]) and o["max_u"] < args.fp64_below]
@@ -423,8 +425,8 @@ def run_sweep(args):
         dt = time.perf_counter() - t0
         sched = b.schedule_report()
         b.close()
-        return dict(t=dt, t_init=t_init, steps=steps32, obs=obs32, ok=ok32, tiny=len(tiny), fallbacks=fallbacks,
-                    schedule=sched)
+        return dict(t=dt, t_init=t_init, t_fp32=t_fp32, steps=steps32, obs=obs32, ok=ok32, tiny=len(tiny),
+                    fallbacks=fallbacks, schedule=sched)
 
     plain = batched_arm(False)
     warm = batched_arm(True) if args.sweep_warm else None
@@ -463,9 +465,11 @@ def run_sweep(args):
     ratio_t = [abs(plain["obs"][i]["max_u"] / obs64[i]["max_u"] - 1.0) for i in fin_t]
     small_t = [i for i in fin_t if max(plain["obs"][i]["max_u"], obs64[i]["max_u"]) < args.fp64_below]
     arms = {"batched_fp32_tanh_s": round(plain["t"], 3),
+            "tanh_fp32_phase_s": round(plain["t_fp32"], 3),
             "diverged_tanh_fp32": sum(1 for o in plain["obs"] if not np.isfinite(o["max_u"]))}
     if warm:
         arms.update({"batched_fp32_warm_s": round(warm["t"], 3), "warm_init_s": round(warm["t_init"], 3),
+                     "warm_fp32_phase_s": round(warm["t_fp32"], 3),
                      "warm_fallbacks": warm["fallbacks"],
                      "steps_total_tanh": int(sum(plain["steps"])), "steps_total_warm": int(sum(warm["steps"]))})
     line = {
