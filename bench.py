@@ -64,10 +64,13 @@ def measured_peak_gbs():
 
 
 def kernel_source_hash():
+    """Hash of the sources that define the single-domain step kernels (the ones
+    the recorded counters describe); the batch, network and API files are not
+    part of it."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1906_11027_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
+        if fn in ("kernels.cuh", "lattice.cuh", "internal.h") or (fn.startswith("kernels_") and fn.endswith(".cu")):
             with open(os.path.join(csrc, fn), "rb") as fh:
                 h.update(fn.encode())
                 h.update(fh.read())

@@ -358,11 +358,12 @@ constexpr int kObsSlices = 8;
 template <class Real>
 __global__ void __launch_bounds__(256) k_batch_obs(const BatchDom* __restrict__ doms, const Real* __restrict__ pool,
                                                    const int* __restrict__ cur_of, const long long pool_stride,
-                                                   double* __restrict__ partials, int ndom)
+                                                   double* __restrict__ partials, int ndom, int only_active)
 {
     const int d = blockIdx.x / kObsSlices, slice = blockIdx.x % kObsSlices;
     if (d >= ndom) return;
     const BatchDom dm = doms[d];
+    if (only_active && !dm.active) return;  // a retired domain keeps its last observables
     const DevParams p = dom_params(dm);
     const Real* A = pool + dm.off + (cur_of[d] ? pool_stride : 0);
     double v[kObsWidth] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -394,10 +395,12 @@ __global__ void __launch_bounds__(256) k_batch_obs(const BatchDom* __restrict__ 
 template <class Real>
 __global__ void k_batch_obs_final(const BatchDom* __restrict__ doms, const Real* __restrict__ pool,
                                   const int* __restrict__ cur_of, const long long pool_stride,
-                                  const double* __restrict__ partials, double* __restrict__ res, int ndom)
+                                  const double* __restrict__ partials, double* __restrict__ res, int ndom,
+                                  int only_active)
 {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= ndom) return;
+    if (only_active && !doms[d].active) return;
     double acc[kObsWidth];
     for (int k = 0; k < kObsWidth; ++k) acc[k] = partials[static_cast<long long>(d) * kObsSlices * kObsWidth + k];
     for (int s = 1; s < kObsSlices; ++s)
@@ -719,23 +722,26 @@ int autotune(lbm_batch* b)
     return select_variant(b, best);
 }
 
-// Observables of every domain into d_res (the state pointed to by d_cur_of).
-cudaError_t launch_obs(lbm_batch* b)
+// Observables into d_res (the state pointed to by d_cur_of): of every domain, or
+// (only_active, inside the steady-check graph) of the domains still stepping.
+cudaError_t launch_obs(lbm_batch* b, int only_active = 0)
 {
     const long long stride = static_cast<const char*>(b->pool[1]) - static_cast<const char*>(b->pool[0]);
     const long long es = b->fp32 ? 4 : 8;
     if (b->fp32) {
         k_batch_obs<float><<<b->n * kObsSlices, 256, 0, b->stream>>>(
-            b->d_doms, static_cast<const float*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials, b->n);
+            b->d_doms, static_cast<const float*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials, b->n,
+            only_active);
         k_batch_obs_final<float><<<(b->n + 63) / 64, 64, 0, b->stream>>>(
             b->d_doms, static_cast<const float*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials, b->d_res,
-            b->n);
+            b->n, only_active);
     } else {
         k_batch_obs<double><<<b->n * kObsSlices, 256, 0, b->stream>>>(
-            b->d_doms, static_cast<const double*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials, b->n);
+            b->d_doms, static_cast<const double*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials, b->n,
+            only_active);
         k_batch_obs_final<double><<<(b->n + 63) / 64, 64, 0, b->stream>>>(
             b->d_doms, static_cast<const double*>(b->pool[0]), b->d_cur_of, stride / es, b->d_partials,
-            b->d_res, b->n);
+            b->d_res, b->n, only_active);
     }
     return cudaGetLastError();
 }
@@ -939,7 +945,7 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < K && e == cudaSuccess; ++i) e = launch_step(b, (b->cur + i) & 1);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_newly, 0, sizeof(int), b->stream);
-        if (e == cudaSuccess) e = launch_obs(b);
+        if (e == cudaSuccess) e = launch_obs(b, 1);
         if (e == cudaSuccess) {
             k_batch_check<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_doms, b->d_res, b->d_prev, b->n, tol,
                                                                     floor_rel, K, b->d_newly);
