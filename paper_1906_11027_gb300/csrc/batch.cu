@@ -36,6 +36,7 @@ constexpr int kQ9 = 9;
 struct BatchDom {
     int nx, ny, order, ntx, nch, active;
     long long off;   // element offset of the domain in each population pool
+    long long poff;  // element offset of the domain in the psi scratch field (two-pass shape)
     double G, omega, pref, rho_bar;
 };
 
@@ -311,6 +312,98 @@ __global__ void __launch_bounds__(TX + 32) k_batch_step_seg(const BatchDom* __re
     if (!ok && threadIdx.x == 0) atomicOr(err, kErrTimeout);
 }
 
+// Two-pass form of the batch step, for few active cells: the march of the other
+// shapes runs its rows one after another, so a step cannot finish faster than
+// one item's march however little work is left.  Here a step is two launches
+// with one thread per cell and no sequential loop: k_batch_psi2 writes psi of
+// every active cell to a scratch field, k_batch_fused2 gathers, takes the force
+// from that field (the same pair order and arithmetic as the ring kernels, so the
+// results are bitwise the same) and collides.  Work item = 256 consecutive cells
+// of one domain.
+template <int ORD, class Real>
+__device__ __forceinline__ void force_global(const Real* __restrict__ psi, int nx, int ny, int x, int y, double G,
+                                             Real (&F)[3])
+{
+    using L = Lattice<kLatD2Q9>;
+    using S = Stencil<2, ORD>;
+    Real ax = Real(0), ay = Real(0), az = Real(0);
+    sfor<S::n / 2>([&](auto kI) {
+        constexpr int a = 2 * decltype(kI)::value;
+        constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1];
+        constexpr double wt = S::T.w[a] * L::cs2;
+        const Real d = psi[wrap_near(y + ey, ny) * nx + wrap_near(x + ex, nx)] -
+                       psi[wrap_near(y - ey, ny) * nx + wrap_near(x - ex, nx)];
+        if (ex != 0) ax += Real(wt * ex) * d;
+        if (ey != 0) ay += Real(wt * ey) * d;
+    });
+    const Real gp = -Real(G) * psi[y * nx + x];
+    F[0] = gp * ax;
+    F[1] = gp * ay;
+    F[2] = gp * az;
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_batch_psi2(const BatchDom* __restrict__ doms, const int4* __restrict__ items,
+                                                    const int* __restrict__ nitems, const Real* __restrict__ pool_in,
+                                                    Real* __restrict__ psi_pool)
+{
+    const int n = *nitems;
+    for (int it = blockIdx.x; it < n; it += gridDim.x) {
+        const int4 w = items[it];
+        const BatchDom d = doms[w.x];
+        const DevParams p = dom_params(d);
+        const long long i = static_cast<long long>(w.y) * 256 + threadIdx.x;
+        if (i >= p.N) continue;
+        const int x = static_cast<int>(i % p.nx), y = static_cast<int>(i / p.nx);
+        Real f[kQ9];
+        gather<kLatD2Q9>(pool_in + d.off, p, x, y, 0, f);
+        Real s = Real(0);
+        sfor<kQ9>([&](auto bI) { s += f[decltype(bI)::value]; });
+        psi_pool[d.poff + i] = psi_of<kLatD2Q9>(std::is_same<Real, float>::value ? Real(p.rho_bar) + s : s, p);
+    }
+}
+
+template <int ORD, class Real>
+__device__ __forceinline__ void fused2_cell(const Real* __restrict__ A, const Real* __restrict__ psi,
+                                            Real* __restrict__ Bo, const DevParams& p, long long i)
+{
+    const int x = static_cast<int>(i % p.nx), y = static_cast<int>(i / p.nx);
+    Real f[kQ9];
+    gather<kLatD2Q9>(A, p, x, y, 0, f);
+    Real F[3];
+    force_global<ORD, Real>(psi, p.nx, p.ny, x, y, p.G, F);
+    collide<kLatD2Q9, 0>(f, F, p);
+    sfor<kQ9>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        Bo[static_cast<long long>(b) * p.N + i] = f[b];
+    });
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_batch_fused2(const BatchDom* __restrict__ doms,
+                                                      const int4* __restrict__ items, const int* __restrict__ nitems,
+                                                      const Real* __restrict__ pool_in,
+                                                      const Real* __restrict__ psi_pool, Real* __restrict__ pool_out)
+{
+    const int n = *nitems;
+    for (int it = blockIdx.x; it < n; it += gridDim.x) {
+        const int4 w = items[it];
+        const BatchDom d = doms[w.x];
+        const DevParams p = dom_params(d);
+        const long long i = static_cast<long long>(w.y) * 256 + threadIdx.x;
+        if (i >= p.N) continue;
+        const Real* A = pool_in + d.off;
+        const Real* psi = psi_pool + d.poff;
+        Real* Bo = pool_out + d.off;
+        switch (d.order) {
+        case 4: fused2_cell<4, Real>(A, psi, Bo, p, i); break;
+        case 6: fused2_cell<6, Real>(A, psi, Bo, p, i); break;
+        case 8: fused2_cell<8, Real>(A, psi, Bo, p, i); break;
+        default: fused2_cell<10, Real>(A, psi, Bo, p, i); break;
+        }
+    }
+}
+
 // Per-cell macroscopic values of domain d at cell i (pulled populations, psi of
 // the neighbourhood recomputed from the populations; used by the observables).
 template <int ORD, class Real>
@@ -499,6 +592,7 @@ struct lbm_batch {
     std::vector<int> retired_at_check;
     long long pool_elems;
     void* pool[2];
+    void* psi_pool;  // psi of every cell, for the two-pass shape
     BatchDom* d_doms;
     int4* d_items;
     int* d_nitems;
@@ -520,6 +614,8 @@ struct lbm_batch {
     unsigned* h_err;  // pinned copy, read after every graph block
     int var;        // tile shape in use (index into the variant table)
     bool tuned;     // autotuner has run, or a shape was pinned
+    bool pinned;    // a shape was pinned by lbm_batch_set_schedule (never re-tuned)
+    long long tuned_cells;  // active cells when the shape was last tuned
     std::vector<double> tune_ms;  // ms per step of each shape (< 0: not timed)
 
     void* dalloc(size_t bytes)
@@ -551,7 +647,8 @@ struct BatchVariant {
     int tx, zc;
     cudaError_t (*launch)(lbm_batch* b, int parity);
     int (*occupancy)(int fp32);
-    bool staged;  // bulk-copy staging: FP32 only, every nx a multiple of 4
+    bool staged;   // bulk-copy staging: FP32 only, every nx a multiple of 4
+    bool per_cell; // two-pass shape: items are 256 consecutive cells, not (tile, row chunk)
 };
 
 template <int TX, int ZC>
@@ -606,18 +703,55 @@ int occupancy_seg(int)
     return occ;
 }
 
+cudaError_t launch_twopass(lbm_batch* b, int parity)
+{
+    if (b->fp32) {
+        k_batch_psi2<float><<<b->grid, 256, 0, b->stream>>>(b->d_doms, b->d_items, b->d_nitems,
+                                                             static_cast<const float*>(b->pool[parity]),
+                                                             static_cast<float*>(b->psi_pool));
+        k_batch_fused2<float><<<b->grid, 256, 0, b->stream>>>(
+            b->d_doms, b->d_items, b->d_nitems, static_cast<const float*>(b->pool[parity]),
+            static_cast<const float*>(b->psi_pool), static_cast<float*>(b->pool[parity ^ 1]));
+    } else {
+        k_batch_psi2<double><<<b->grid, 256, 0, b->stream>>>(b->d_doms, b->d_items, b->d_nitems,
+                                                              static_cast<const double*>(b->pool[parity]),
+                                                              static_cast<double*>(b->psi_pool));
+        k_batch_fused2<double><<<b->grid, 256, 0, b->stream>>>(
+            b->d_doms, b->d_items, b->d_nitems, static_cast<const double*>(b->pool[parity]),
+            static_cast<const double*>(b->psi_pool), static_cast<double*>(b->pool[parity ^ 1]));
+    }
+    return cudaGetLastError();
+}
+
+int occupancy_twopass(int fp32)
+{
+    int a = 0, c = 0;
+    if (fp32) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_psi2<float>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_batch_fused2<float>, 256, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_psi2<double>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_batch_fused2<double>, 256, 0);
+    }
+    return std::min(a, c);
+}
+
 const BatchVariant kBatchVariants[] = {
-    {"tile64_rows16", 64, 16, &launch_variant<64, 16>, &occupancy_variant<64, 16>, false},
-    {"tile32_rows16", 32, 16, &launch_variant<32, 16>, &occupancy_variant<32, 16>, false},
-    {"tile32_rows32", 32, 32, &launch_variant<32, 32>, &occupancy_variant<32, 32>, false},
-    {"tile64_rows8", 64, 8, &launch_variant<64, 8>, &occupancy_variant<64, 8>, false},
-    {"tile64_rows32", 64, 32, &launch_variant<64, 32>, &occupancy_variant<64, 32>, false},
-    {"tile128_rows16", 128, 16, &launch_variant<128, 16>, &occupancy_variant<128, 16>, false},
-    {"tile128_rows32", 128, 32, &launch_variant<128, 32>, &occupancy_variant<128, 32>, false},
-    {"staged64_rows32", 64, 32, &launch_seg<64, 32, 8>, &occupancy_seg<64, 32, 8>, true},
-    {"staged128_rows32", 128, 32, &launch_seg<128, 32, 8>, &occupancy_seg<128, 32, 8>, true},
-    {"staged128_rows64", 128, 64, &launch_seg<128, 64, 8>, &occupancy_seg<128, 64, 8>, true},
-    {"staged256_rows64", 256, 64, &launch_seg<256, 64, 8>, &occupancy_seg<256, 64, 8>, true},
+    {"tile64_rows16", 64, 16, &launch_variant<64, 16>, &occupancy_variant<64, 16>, false, false},
+    {"tile32_rows16", 32, 16, &launch_variant<32, 16>, &occupancy_variant<32, 16>, false, false},
+    {"tile32_rows32", 32, 32, &launch_variant<32, 32>, &occupancy_variant<32, 32>, false, false},
+    {"tile64_rows8", 64, 8, &launch_variant<64, 8>, &occupancy_variant<64, 8>, false, false},
+    {"tile64_rows32", 64, 32, &launch_variant<64, 32>, &occupancy_variant<64, 32>, false, false},
+    {"tile128_rows16", 128, 16, &launch_variant<128, 16>, &occupancy_variant<128, 16>, false, false},
+    {"tile128_rows32", 128, 32, &launch_variant<128, 32>, &occupancy_variant<128, 32>, false, false},
+    {"staged64_rows32", 64, 32, &launch_seg<64, 32, 8>, &occupancy_seg<64, 32, 8>, true, false},
+    {"staged128_rows32", 128, 32, &launch_seg<128, 32, 8>, &occupancy_seg<128, 32, 8>, true, false},
+    {"staged128_rows64", 128, 64, &launch_seg<128, 64, 8>, &occupancy_seg<128, 64, 8>, true, false},
+    {"staged256_rows64", 256, 64, &launch_seg<256, 64, 8>, &occupancy_seg<256, 64, 8>, true, false},
+    {"staged64_rows1024", 64, 1024, &launch_seg<64, 1024, 8>, &occupancy_seg<64, 1024, 8>, true, false},
+    {"staged128_rows1024", 128, 1024, &launch_seg<128, 1024, 8>, &occupancy_seg<128, 1024, 8>, true, false},
+    {"tile32_rows8", 32, 8, &launch_variant<32, 8>, &occupancy_variant<32, 8>, false, false},
+    {"twopass_cells256", 256, 1, &launch_twopass, &occupancy_twopass, false, true},
 };
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 constexpr int kMinTX = 32, kMinZC = 8;  // smallest tile and chunk of the table (item buffer size)
@@ -641,9 +775,17 @@ int rebuild_items(lbm_batch* b)
         m.ntx = (m.nx + v.tx - 1) / v.tx;
         m.nch = (m.ny + v.zc - 1) / v.zc;
         if (!m.active) continue;
+        if (v.per_cell) {
+            const long long nb = (static_cast<long long>(m.nx) * m.ny + 255) / 256;
+            for (long long k = 0; k < nb; ++k) items.push_back(make_int4(d, static_cast<int>(k), 0, 1));
+            continue;
+        }
         for (int c = 0; c < m.nch; ++c)
-            for (int t = 0; t < m.ntx; ++t) items.push_back(make_int4(d, t, c, 0));
+            for (int t = 0; t < m.ntx; ++t)
+                items.push_back(make_int4(d, t, c, std::min(v.zc, m.ny - c * v.zc)));  // w: rows of the item
     }
+    // longest items first: the persistent blocks take them in index order
+    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& c) { return a.w > c.w; });
     b->nitems = static_cast<int>(items.size());
     if (!items.empty())
         LBM_BCK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
@@ -671,19 +813,46 @@ int select_variant(lbm_batch* b, int v)
             cudaGraphExecDestroy(b->graph[k]);
             b->graph[k] = nullptr;
         }
-    return rebuild_items(b);
+    if (int rc = rebuild_items(b)) return rc;
+    // no more persistent blocks than items: the work list only shrinks until the
+    // next selection, and the blocks loop over whatever it holds
+    b->grid = std::max(1, std::min(b->grid, b->nitems));
+    return LBM_OK;
 }
 
 // Times every shape on the batch's current state (a few steps each, from a saved
 // copy that is put back afterwards, so the state does not advance) and keeps the
 // fastest.  Without room for the copy the default shape stays.
-int autotune(lbm_batch* b)
+int autotune(lbm_batch* b, bool again = false)
 {
-    if (b->tuned) return LBM_OK;
+    if (b->tuned && !(again && !b->pinned)) return LBM_OK;
     b->tuned = true;
-    const size_t bytes = (b->fp32 ? 4 : 8) * static_cast<size_t>(b->pool_elems);
-    void* save = b->dalloc(bytes);
+    // the active domains' states are saved and put back (retired ones are not stepped)
+    const size_t es = b->fp32 ? 4 : 8;
+    size_t bytes = 0;
+    long long cells = 0;
+    for (const auto& m : b->doms)
+        if (m.active) {
+            bytes += es * kQ9 * static_cast<size_t>(m.nx) * m.ny;
+            cells += static_cast<long long>(m.nx) * m.ny;
+        }
+    b->tuned_cells = cells;
+    if (bytes == 0) return LBM_OK;
+    char* save = static_cast<char*>(b->dalloc(bytes));
     if (!save) return LBM_OK;
+    auto copy_states = [&](bool to_save) {
+        size_t o = 0;
+        for (const auto& m : b->doms) {
+            if (!m.active) continue;
+            const size_t n = es * kQ9 * static_cast<size_t>(m.nx) * m.ny;
+            char* pool = static_cast<char*>(b->pool[b->cur]) + es * m.off;
+            cudaError_t e = to_save ? cudaMemcpyAsync(save + o, pool, n, cudaMemcpyDeviceToDevice, b->stream)
+                                    : cudaMemcpyAsync(pool, save + o, n, cudaMemcpyDeviceToDevice, b->stream);
+            if (e != cudaSuccess) return e;
+            o += n;
+        }
+        return cudaSuccess;
+    };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = LBM_OK;
     auto ck = [&](cudaError_t e) {
@@ -691,7 +860,7 @@ int autotune(lbm_batch* b)
     };
     ck(cudaEventCreate(&e0));
     ck(cudaEventCreate(&e1));
-    ck(cudaMemcpyAsync(save, b->pool[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
+    ck(copy_states(true));
     constexpr int kWarm = 2, kTimed = 8;
     b->tune_ms.assign(kNumBatchVariants, -1.0);
     bool nx4 = true;
@@ -712,7 +881,7 @@ int autotune(lbm_batch* b)
         ck(cudaEventElapsedTime(&ms, e0, e1));
         b->tune_ms[v] = ms / kTimed;
         if (b->tune_ms[v] < b->tune_ms[best]) best = v;
-        ck(cudaMemcpyAsync(b->pool[b->cur], save, bytes, cudaMemcpyDeviceToDevice, b->stream));
+        ck(copy_states(false));
     }
     ck(cudaStreamSynchronize(b->stream));
     if (e0) cudaEventDestroy(e0);
@@ -788,7 +957,7 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
         cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
         b->own_stream = true;
     }
-    long long off = 0;
+    long long off = 0, poff = 0;
     b->doms.resize(n);
     for (int d = 0; d < n; ++d) {
         const lbm_params& p = ps[d];
@@ -824,6 +993,8 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
         }
         off += (long long)kQ9 * p.nx * p.ny;
         off = (off + 63) / 64 * 64;  // 256-byte aligned domains
+        m.poff = poff;
+        poff += ((long long)p.nx * p.ny + 63) / 64 * 64;
     }
     b->pool_elems = off;
     const size_t es = fp32 ? 4 : 8;
@@ -831,6 +1002,7 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
     for (auto& m : b->doms) items += (long long)m.ntx * m.nch;
     b->pool[0] = b->dalloc(es * off);
     b->pool[1] = b->dalloc(es * off);
+    b->psi_pool = b->dalloc(es * poff);
     b->d_doms = static_cast<BatchDom*>(b->dalloc(sizeof(BatchDom) * n));
     b->d_items = static_cast<int4*>(b->dalloc(sizeof(int4) * items));
     b->d_nitems = static_cast<int*>(b->dalloc(256));
@@ -841,7 +1013,7 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
     b->d_prev = static_cast<double*>(b->dalloc(sizeof(double) * n));
     b->d_newly = static_cast<int*>(b->dalloc(256));
     b->d_err = static_cast<unsigned*>(b->dalloc(256));
-    if (!b->pool[0] || !b->pool[1] || !b->d_doms || !b->d_items || !b->d_nitems || !b->d_cur_of || !b->d_init ||
+    if (!b->pool[0] || !b->pool[1] || !b->psi_pool || !b->d_doms || !b->d_items || !b->d_nitems || !b->d_cur_of || !b->d_init ||
         !b->d_partials || !b->d_res || !b->d_prev || !b->d_newly || !b->d_err) {
         lbm_batch_destroy(b);
         return set_last_error(LBM_ENOMEM, "lbm_batch_create: device allocation failed");
@@ -888,6 +1060,7 @@ int lbm_batch_destroy(lbm_batch* b)
         if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
     b->dfree(b->pool[0]);
     b->dfree(b->pool[1]);
+    b->dfree(b->psi_pool);
     b->dfree(b->d_doms);
     b->dfree(b->d_items);
     b->dfree(b->d_nitems);
@@ -937,6 +1110,7 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t
     const double floor_rel = b->fp32 ? 1e-6 : 0.0;
     // one graph per starting parity is not needed: K is even, so every block of K
     // steps starts from the same parity
+    auto capture = [&]() -> int {
     if (!b->graph[0] || b->graph_k != K || b->graph_cur != b->cur) {
         if (b->graph[0]) cudaGraphExecDestroy(b->graph[0]);
         b->graph[0] = nullptr;
@@ -964,6 +1138,9 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t
         b->graph_k = K;
         b->graph_cur = b->cur;
     }
+    return LBM_OK;
+    };
+    if (int rc = capture()) return rc;
     // the observables inside the graph read cur_of: active domains end each block
     // on the same parity as they started (K even)
     for (int d = 0; d < b->n; ++d)
@@ -991,6 +1168,15 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t
             nactive = 0;
             for (auto& m : b->doms) nactive += m.active;
             if (int rc = rebuild_items(b)) return rc;
+            // when the active set has shrunk eightfold, finer items may fill the GPU
+            // better: time the shapes again on what is left
+            long long cells = 0;
+            for (const auto& m : b->doms)
+                if (m.active) cells += static_cast<long long>(m.nx) * m.ny;
+            if (nactive > 0 && cells * 8 < b->tuned_cells) {
+                if (int rc = autotune(b, true)) return rc;
+                if (int rc = capture()) return rc;
+            }
         }
     }
     LBM_BCK(launch_obs(b));
@@ -1045,6 +1231,7 @@ int lbm_batch_set_schedule(lbm_batch* b, const char* name)
             if (kBatchVariants[v].staged && !(b->fp32 && nx4))
                 return set_last_error(LBM_EINVAL, "lbm_batch_set_schedule: staged shapes need FP32 and nx % 4 == 0");
             b->tuned = true;
+            b->pinned = true;
             return select_variant(b, v);
         }
     return set_last_error(LBM_EINVAL, "lbm_batch_set_schedule: unknown tile shape");
