@@ -653,7 +653,9 @@ int lbm_init_droplet_learned(lbm_ctx* c, lbm_mlp* net, double R, double rho_l, d
     if (rc != LBM_OK) return rc;
     bool ok = std::isfinite(mlo) && std::isfinite(mhi) && (mlo - m0) * (mhi - m0) < 0.0;
     double Re = R;
-    for (int it = 0; ok && it < 48; ++it) {
+    // 36 halvings of a bracket of at most a few hundred cells leave R_eff within
+    // 1e-8; the uniform shift below removes the remaining mass difference
+    for (int it = 0; ok && it < 36; ++it) {
         Re = 0.5 * (lo + hi);
         double mm = 0.0;
         if (int r2 = mass_at(Re, &mm)) return r2;

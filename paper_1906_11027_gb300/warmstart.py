@@ -80,7 +80,9 @@ def batch_warm_init(batch, domains, net):
     Returns the number of domains that kept the tanh start."""
     fallbacks = 0
     for i, d in enumerate(domains):
-        dom = lbm.Domain(d["nx"], d["ny"], G=d["G"], tau=d["tau"], stencil=d["stencil"], precision=lbm.LBM_FP64)
+        # the caching allocator keeps the per-domain set-up free of cudaMalloc/cudaFree
+        dom = lbm.Domain(d["nx"], d["ny"], G=d["G"], tau=d["tau"], stencil=d["stencil"], precision=lbm.LBM_FP64,
+                         torch_alloc=True)
         fb, _ = dom.init_droplet_learned(net, d["R"], d["rho_l"], d["rho_g"], d["width"])
         if fb:
             fallbacks += 1
