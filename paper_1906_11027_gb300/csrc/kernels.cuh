@@ -817,6 +817,187 @@ __global__ void __launch_bounds__(NX * TY + (PROD ? 32 : 0), 1)
     if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
 }
 
+// Persistent form of the whole-row schedule: one block per SM walks the
+// (row pair, chunk) items chunk-major with stride gridDim.x, so the blocks that
+// run at a time still cover neighbouring row pairs at similar z (their shared
+// halo rows meet in L2).  The producer warp issues one global sequence of slabs
+// across the block's items: as soon as the last slabs of an item are consumed it
+// runs on into the next item's first slabs, which load while the current item's
+// last rows collide, so the copy stream never restarts from empty.
+template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int NSTG>
+__global__ void __launch_bounds__(NX * TY + 32, 1)
+    k_onepass_rowp(const __grid_constant__ Pops<Real, Lattice<LAT>::Q> P, DevParams p, int zc, int nitems)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<3, ORD>;
+    constexpr int R = S::radius;
+    constexpr int Q = L::Q;
+    static_assert(L::D == 3 && R == 1 && L::reach == 1, "row staging is written for 3-D radius-1 stencils");
+    constexpr int NT = NX * TY;
+    constexpr int EY = TY + 2 * R;
+    constexpr int EX = NX + 2 * R;
+    constexpr int E = EX * EY;
+    constexpr int NS = 2 * R + 2;
+    constexpr int STG = Q * EY * NX;
+    static_assert(NT % 32 == 0 && NT <= 1024 && NSTG >= 2 * R && NSTG <= 32, "block / stages");
+    static_assert((NX * sizeof(Real)) % 16 == 0, "16-byte rows");
+    __shared__ Real ring[NS * E];
+    __shared__ alignas(8) unsigned long long bars[NSTG];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    Real* stage = reinterpret_cast<Real*>(dyn_smem);  // [NSTG][STG]
+
+    const int nty = (p.ny + TY - 1) / TY;
+    const int nm = p.nz;
+    const int plane = NX * p.ny;
+    const int tid = threadIdx.x;
+    const int tx = tid % NX, ty = tid / NX;
+    const int lane = tid & 31;
+    const bool producer = tid >= NT;
+
+    if (tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    int cby = 0, cbz = 0;
+    const Real* src_b = nullptr;
+    sfor<Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int vy = L::T.v[b][1], vz = L::T.v[b][2];
+        if (lane == b) {
+            cby = vy;
+            cbz = vz;
+            src_b = P.in[b];
+        }
+    });
+    // producer: the next slab of the block's global sequence
+    int p_it = blockIdx.x, p_y0 = 0, p_next = 0, p_last = -1;
+    auto p_load_item = [&]() {
+        if (p_it >= nitems) return;
+        const int m0 = (p_it / nty) * zc;
+        const int m1 = (m0 + zc < nm) ? m0 + zc : nm;
+        p_y0 = (p_it % nty) * TY;
+        p_next = m0 - R;
+        p_last = m1 - 1 + R;
+    };
+    p_load_item();
+    long long issued = 0;
+    auto issue_next = [&]() {
+        const int slot = static_cast<int>(issued % NSTG);
+        const uint32_t bar = smem_u32(&bars[slot]);
+        if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(STG * sizeof(Real)));
+        __syncwarp();
+        if (lane < Q) {
+            fence_proxy_async_smem();
+            const Real* pl = src_b + static_cast<long long>(wrap_any(p_next - cbz, nm)) * plane;
+            uint32_t dst = smem_u32(stage + slot * STG + lane * (EY * NX));
+            int y = p_y0 - R - cby, left = EY;
+            while (left > 0) {
+                const int yw = wrap_any(y, p.ny);
+                const int n = (p.ny - yw < left) ? p.ny - yw : left;
+                bulk_g2s(dst, pl + static_cast<long long>(yw) * NX, static_cast<uint32_t>(n * NX * sizeof(Real)), bar);
+                dst += static_cast<uint32_t>(n * NX * sizeof(Real));
+                y += n;
+                left -= n;
+            }
+        }
+        ++issued;
+        if (++p_next > p_last) {
+            p_it += gridDim.x;
+            p_load_item();
+        }
+    };
+    // a slot is refilled once the slab NSTG earlier in the sequence is consumed
+    auto issue_upto = [&](long long consumed) {
+        while (p_it < nitems && issued < consumed + NSTG) issue_next();
+    };
+
+    uint32_t phase = 0;
+    bool ok = true;
+    long long consumed = 0;  // the same count in every thread
+    auto wait_seq = [&](long long q) -> const Real* {
+        const int slot = static_cast<int>(q % NSTG);
+        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        phase ^= 1u << slot;
+        return stage + slot * STG;
+    };
+    const int xm = (tx + 1 == NX) ? 0 : tx + 1;   // c_x = -1
+    const int xp = (tx == 0) ? NX - 1 : tx - 1;   // c_x = +1
+    auto load_cell = [&](const Real* st, int fy, Real (&f)[Q]) {
+        const Real* r = st + fy * NX;
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int vx = L::T.v[b][0];
+            const int c = vx == 0 ? tx : (vx > 0 ? xp : xm);
+            f[b] = r[b * (EY * NX) + c];
+        });
+    };
+    auto rho_psi = [&](const Real (&f)[Q]) {
+        Real sum = Real(0);
+        sfor<Q>([&](auto bI) { sum += f[decltype(bI)::value]; });
+        const Real rho = std::is_same<Real, float>::value ? Real(p.rho_bar) + sum : sum;
+        return psi_of<LAT>(rho, p);
+    };
+    Real fcur[Q], fnxt[Q];
+    auto put_psi = [&](Real* dst, int fy, Real v) {
+        Real* row = dst + fy * EX;
+        row[tx + R] = v;
+        if (tx == 0) row[NX + R] = v;
+        if (tx == NX - 1) row[0] = v;
+    };
+    auto psi_slab = [&](int s, long long q) {
+        const Real* st = wait_seq(q);
+        Real* dst = ring + ring_slot(s, NS) * E;
+        load_cell(st, ty + R, fnxt);
+        put_psi(dst, ty + R, rho_psi(fnxt));
+        for (int k = ty; k < 2 * R; k += TY) {
+            const int fy = (k < R) ? k : EY - 2 * R + k;
+            Real f[Q];
+            load_cell(st, fy, f);
+            put_psi(dst, fy, rho_psi(f));
+        }
+    };
+
+    if (producer) issue_upto(0);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int y0 = (it % nty) * TY;
+        const int m0 = (it / nty) * zc;
+        const int m1 = (m0 + zc < nm) ? m0 + zc : nm;
+        if (!producer)
+            for (int s = m0 - R; s < m0 + R; ++s) psi_slab(s, consumed + (s - (m0 - R)));
+        consumed += 2 * R;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+        __syncthreads();
+        if (producer) issue_upto(consumed);
+        const bool active = !producer && (y0 + ty) < p.ny;
+        const int cell_xy = (y0 + ty) * NX + tx;
+        for (int m = m0; m < m1; ++m) {
+            if (!producer) psi_slab(m + R, consumed);
+            ++consumed;
+            __syncthreads();
+            // every thread is past psi of slab m + R: its stage can be refilled, and
+            // after the item's last slab the next item's first slabs start loading
+            if (producer) issue_upto(consumed);
+            if (active) {
+                Real F[3];
+                force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, ty + R, p.G, F);
+                collide<LAT, COLL>(fcur, F, p);
+                const int c = m * plane + cell_xy;
+                sfor<Q>([&](auto bI) {
+                    constexpr int b = decltype(bI)::value;
+                    __stcs(P.out[b] + c, fcur[b]);
+                });
+            }
+#pragma unroll
+            for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+        }
+        __syncthreads();  // the ring is reused by the next item
+    }
+    if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
+}
+
 // One-pass schedule with bulk-copy staging for 2-D lattices of reach 1 (D2Q9),
 // any force stencil up to radius 3.  A tile is TX cells of a row; the march runs
 // along y.  For row s, direction b needs row s - c_by over x0 - XP .. x0 + TX + XP
@@ -1819,6 +2000,43 @@ cudaError_t launch_onepass(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int NSTG>
+cudaError_t launch_onepass_rowp(const LaunchArgs& a, cudaStream_t s)
+{
+    constexpr size_t dyn = sizeof(Real) * NSTG * Lattice<LAT>::Q * (TY + 2) * NX;
+    auto kern = &k_onepass_rowp<LAT, ORD, COLL, Real, NX, TY, NSTG>;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.p.nx != NX) return cudaErrorInvalidValue;
+    const int nty = (a.p.ny + TY - 1) / TY;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // one block per SM: the chunk count that minimises the largest number of
+    // slabs a block marches (its items x (chunk + the two warm-up slabs))
+    int zc = a.p.nz;
+    long long best = -1;
+    for (int nc = 1; nc <= a.p.nz; ++nc) {
+        const int len = (a.p.nz + nc - 1) / nc;
+        const int used = (a.p.nz + len - 1) / len;
+        const long long per_block = (static_cast<long long>(nty) * used + nsm - 1) / nsm;
+        const long long cost = per_block * (len + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            zc = len;
+        }
+    }
+    const int nitems = nty * ((a.p.nz + zc - 1) / zc);
+    const int grid = nitems < nsm ? nitems : nsm;
+    const auto P = make_pops<Real, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
+    kern<<<grid, NX * TY + 32, dyn, s>>>(P, a.p, zc, nitems);
+    return cudaGetLastError();
+}
+
 template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int ZC, int NSTG, int PROD>
 cudaError_t launch_onepass_row(const LaunchArgs& a, cudaStream_t s)
 {
@@ -2062,6 +2280,7 @@ KernelSet make_set()
                 add("onepass_row256x2_z32_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 32, 2, 1>, 1, 256);
                 add("onepass_row256x2_zauto_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 0, 2, 1>, 1, 256);
                 add("onepass_row256x2_zauto_s2_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 0, 2, 2>, 1, 256);
+                add("onepass_rowp256x2_s2", &launch_onepass_rowp<LAT, ORD, COLL, Real, 256, 2, 2>, 1, 256);
                 add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 0>, 1, 128);
                 add("onepass_row128x4_z32_s3_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 1>, 1, 128);
                 add("onepass_row128x4_zauto_s3_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 0, 3, 2>, 1, 128);
