@@ -1528,6 +1528,205 @@ __device__ __forceinline__ void collide2_bgk(float2 (&f)[Lattice<LAT>::Q], const
     });
 }
 
+// Packed-pair form of the persistent whole-row schedule (FP32 BGK): a compute
+// thread owns the x-adjacent cells (2t, 2t + 1) of one row, so the directions
+// with c_x = 0 come from shared memory as one 8-byte load per pair, the force and
+// collision run on float2 pairs with the packed FP32 instructions, and every
+// store is one 8-byte store.  Staging, item walk and producer are those of
+// k_onepass_rowp.
+template <int LAT, int ORD, int NX, int TY, int NSTG>
+__global__ void __launch_bounds__(NX / 2 * TY + 32, 1)
+    k_onepass_rowp2(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, int zc, int nitems)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<3, ORD>;
+    constexpr int R = S::radius;
+    constexpr int Q = L::Q;
+    static_assert(L::D == 3 && R == 1 && L::reach == 1, "row staging is written for 3-D radius-1 stencils");
+    constexpr int NT = NX / 2 * TY;  // compute threads
+    constexpr int EY = TY + 2 * R;
+    constexpr int EX = NX + 2 * R;
+    constexpr int E = EX * EY;
+    constexpr int NS = 2 * R + 2;
+    constexpr int STG = Q * EY * NX;
+    static_assert(NT % 32 == 0 && NT + 32 <= 1024 && NSTG >= 2 * R && NSTG <= 32 && NX % 4 == 0, "block / stages");
+    __shared__ float ring[NS * E];
+    __shared__ alignas(8) unsigned long long bars[NSTG];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    float* stage = reinterpret_cast<float*>(dyn_smem);  // [NSTG][STG]
+
+    const int nty = (p.ny + TY - 1) / TY;
+    const int nm = p.nz;
+    const int plane = NX * p.ny;
+    const int tid = threadIdx.x;
+    const int tp = tid % (NX / 2), ty = tid / (NX / 2);  // pair index along x, row in the tile
+    const int x0 = 2 * tp;                               // first cell of the pair
+    const int lane = tid & 31;
+    const bool producer = tid >= NT;
+
+    if (tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    int cby = 0, cbz = 0;
+    const float* src_b = nullptr;
+    sfor<Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int vy = L::T.v[b][1], vz = L::T.v[b][2];
+        if (lane == b) {
+            cby = vy;
+            cbz = vz;
+            src_b = P.in[b];
+        }
+    });
+    int p_it = blockIdx.x, p_y0 = 0, p_next = 0, p_last = -1;
+    auto p_load_item = [&]() {
+        if (p_it >= nitems) return;
+        const int m0 = (p_it / nty) * zc;
+        const int m1 = (m0 + zc < nm) ? m0 + zc : nm;
+        p_y0 = (p_it % nty) * TY;
+        p_next = m0 - R;
+        p_last = m1 - 1 + R;
+    };
+    p_load_item();
+    long long issued = 0;
+    auto issue_next = [&]() {
+        const int slot = static_cast<int>(issued % NSTG);
+        const uint32_t bar = smem_u32(&bars[slot]);
+        if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(STG * sizeof(float)));
+        __syncwarp();
+        if (lane < Q) {
+            fence_proxy_async_smem();
+            const float* pl = src_b + static_cast<long long>(wrap_any(p_next - cbz, nm)) * plane;
+            uint32_t dst = smem_u32(stage + slot * STG + lane * (EY * NX));
+            int y = p_y0 - R - cby, left = EY;
+            while (left > 0) {
+                const int yw = wrap_any(y, p.ny);
+                const int n = (p.ny - yw < left) ? p.ny - yw : left;
+                bulk_g2s(dst, pl + static_cast<long long>(yw) * NX, static_cast<uint32_t>(n * NX * sizeof(float)), bar);
+                dst += static_cast<uint32_t>(n * NX * sizeof(float));
+                y += n;
+                left -= n;
+            }
+        }
+        ++issued;
+        if (++p_next > p_last) {
+            p_it += gridDim.x;
+            p_load_item();
+        }
+    };
+    auto issue_upto = [&](long long consumed) {
+        while (p_it < nitems && issued < consumed + NSTG) issue_next();
+    };
+
+    uint32_t phase = 0;
+    bool ok = true;
+    long long consumed = 0;
+    auto wait_seq = [&](long long q) -> const float* {
+        const int slot = static_cast<int>(q % NSTG);
+        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        phase ^= 1u << slot;
+        return stage + slot * STG;
+    };
+    // pull columns of the pair for c_x = +1 (x - 1) and c_x = -1 (x + 1), periodic
+    const int xl = (x0 == 0) ? NX - 1 : x0 - 1;        // left of the first cell
+    const int xr = (x0 + 2 == NX) ? 0 : x0 + 2;        // right of the second cell
+    auto load_pair = [&](const float* st, int fy, float2 (&f)[Q]) {
+        const float* r = st + fy * NX;
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int vx = L::T.v[b][0];
+            const float* rb = r + b * (EY * NX);
+            if (vx == 0)
+                f[b] = *reinterpret_cast<const float2*>(rb + x0);
+            else if (vx > 0)
+                f[b] = make_float2(rb[xl], rb[x0]);
+            else
+                f[b] = make_float2(rb[x0 + 1], rb[xr]);
+        });
+    };
+    auto rho_psi2 = [&](const float2 (&f)[Q]) {
+        float2 sum = p2(0.f);
+        sfor<Q>([&](auto bI) { sum = add2(sum, f[decltype(bI)::value]); });
+        const float rb = static_cast<float>(p.rho_bar);
+        return make_float2(psi_of<LAT>(rb + sum.x, p), psi_of<LAT>(rb + sum.y, p));
+    };
+    float2 fcur[Q], fnxt[Q];
+    auto put_psi2 = [&](float* dst, int fy, float2 v) {
+        float* row = dst + fy * EX;
+        row[x0 + R] = v.x;
+        row[x0 + 1 + R] = v.y;
+        if (x0 == 0) row[NX + R] = v.x;          // wrapped column right of the row
+        if (x0 + 2 == NX) row[0] = v.y;          // wrapped column left of the row
+    };
+    auto psi_slab = [&](int s, long long q) {
+        const float* st = wait_seq(q);
+        float* dst = ring + ring_slot(s, NS) * E;
+        load_pair(st, ty + R, fnxt);
+        put_psi2(dst, ty + R, rho_psi2(fnxt));
+        for (int k = ty; k < 2 * R; k += TY) {
+            const int fy = (k < R) ? k : EY - 2 * R + k;
+            float2 f[Q];
+            load_pair(st, fy, f);
+            put_psi2(dst, fy, rho_psi2(f));
+        }
+    };
+
+    if (producer) issue_upto(0);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int y0 = (it % nty) * TY;
+        const int m0 = (it / nty) * zc;
+        const int m1 = (m0 + zc < nm) ? m0 + zc : nm;
+        if (!producer)
+            for (int s = m0 - R; s < m0 + R; ++s) psi_slab(s, consumed + (s - (m0 - R)));
+        consumed += 2 * R;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+        __syncthreads();
+        if (producer) issue_upto(consumed);
+        const bool active = !producer && (y0 + ty) < p.ny;
+        const int cell_xy = (y0 + ty) * NX + x0;
+        for (int m = m0; m < m1; ++m) {
+            if (!producer) psi_slab(m + R, consumed);
+            ++consumed;
+            __syncthreads();
+            if (producer) issue_upto(consumed);
+            if (active) {
+                // force (Eq. 1) of both cells from the psi ring, opposite vectors paired
+                const float* base[2 * R + 1];
+#pragma unroll
+                for (int k = 0; k < 2 * R + 1; ++k) base[k] = ring + ring_slot(m - R + k, NS) * E + (ty + R) * EX + x0 + R;
+                float2 ax = p2(0.f), ay = p2(0.f), az = p2(0.f);
+                sfor<S::n / 2>([&](auto kI) {
+                    constexpr int a = 2 * decltype(kI)::value;
+                    constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1], ez = S::T.v[a][2];
+                    constexpr double wt = S::T.w[a] * L::cs2;
+                    const float* pp = base[ez + R] + ey * EX + ex;
+                    const float* pm = base[R - ez] - ey * EX - ex;
+                    const float2 d = sub2(make_float2(pp[0], pp[1]), make_float2(pm[0], pm[1]));
+                    if (ex != 0) ax = fma2(p2(float(wt * ex)), d, ax);
+                    if (ey != 0) ay = fma2(p2(float(wt * ey)), d, ay);
+                    if (ez != 0) az = fma2(p2(float(wt * ez)), d, az);
+                });
+                const float2 gp = mul2(p2(float(-p.G)), make_float2(base[R][0], base[R][1]));
+                const float2 F[3] = {mul2(gp, ax), mul2(gp, ay), mul2(gp, az)};
+                collide2_bgk<LAT>(fcur, F, p);
+                const int c = m * plane + cell_xy;
+                sfor<Q>([&](auto bI) {
+                    constexpr int b = decltype(bI)::value;
+                    __stcs(reinterpret_cast<float2*>(P.out[b] + c), fcur[b]);
+                });
+            }
+#pragma unroll
+            for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
+        }
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
+}
+
 template <int LAT, int ORD, int TX2, int TY, int ZC, int MINB, int ST>
 __global__ void __launch_bounds__(TX2 * TY, MINB)
     k_onepass_x2(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, int ntx, int nty)
@@ -2000,6 +2199,50 @@ cudaError_t launch_onepass(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Chunk length of the persistent whole-row schedules (one block per SM): the
+// chunk count that minimises the largest number of slabs a block marches, its
+// items x (chunk + the two warm-up slabs).
+inline int rowp_chunk(int nz, int nty, int nsm)
+{
+    int zc = nz;
+    long long best = -1;
+    for (int nc = 1; nc <= nz; ++nc) {
+        const int len = (nz + nc - 1) / nc;
+        const int used = (nz + len - 1) / len;
+        const long long per_block = (static_cast<long long>(nty) * used + nsm - 1) / nsm;
+        const long long cost = per_block * (len + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            zc = len;
+        }
+    }
+    return zc;
+}
+
+template <int LAT, int ORD, int NX, int TY, int NSTG>
+cudaError_t launch_onepass_rowp2(const LaunchArgs& a, cudaStream_t s)
+{
+    constexpr size_t dyn = sizeof(float) * NSTG * Lattice<LAT>::Q * (TY + 2) * NX;
+    auto kern = &k_onepass_rowp2<LAT, ORD, NX, TY, NSTG>;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.p.nx != NX) return cudaErrorInvalidValue;
+    const int nty = (a.p.ny + TY - 1) / TY;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int zc = rowp_chunk(a.p.nz, nty, nsm);
+    const int nitems = nty * ((a.p.nz + zc - 1) / zc);
+    const int grid = nitems < nsm ? nitems : nsm;
+    const auto P = make_pops<float, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
+    kern<<<grid, NX / 2 * TY + 32, dyn, s>>>(P, a.p, zc, nitems);
+    return cudaGetLastError();
+}
+
 template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int NSTG>
 cudaError_t launch_onepass_rowp(const LaunchArgs& a, cudaStream_t s)
 {
@@ -2016,20 +2259,7 @@ cudaError_t launch_onepass_rowp(const LaunchArgs& a, cudaStream_t s)
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    // one block per SM: the chunk count that minimises the largest number of
-    // slabs a block marches (its items x (chunk + the two warm-up slabs))
-    int zc = a.p.nz;
-    long long best = -1;
-    for (int nc = 1; nc <= a.p.nz; ++nc) {
-        const int len = (a.p.nz + nc - 1) / nc;
-        const int used = (a.p.nz + len - 1) / len;
-        const long long per_block = (static_cast<long long>(nty) * used + nsm - 1) / nsm;
-        const long long cost = per_block * (len + 2);
-        if (best < 0 || cost < best) {
-            best = cost;
-            zc = len;
-        }
-    }
+    const int zc = rowp_chunk(a.p.nz, nty, nsm);
     const int nitems = nty * ((a.p.nz + zc - 1) / zc);
     const int grid = nitems < nsm ? nitems : nsm;
     const auto P = make_pops<Real, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
@@ -2281,6 +2511,7 @@ KernelSet make_set()
                 add("onepass_row256x2_zauto_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 0, 2, 1>, 1, 256);
                 add("onepass_row256x2_zauto_s2_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 0, 2, 2>, 1, 256);
                 add("onepass_rowp256x2_s2", &launch_onepass_rowp<LAT, ORD, COLL, Real, 256, 2, 2>, 1, 256);
+                add("onepass_rowp2_256x2_s2", &launch_onepass_rowp2<LAT, ORD, 256, 2, 2>, 1, 256);
                 add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 0>, 1, 128);
                 add("onepass_row128x4_z32_s3_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 1>, 1, 128);
                 add("onepass_row128x4_zauto_s3_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 0, 3, 2>, 1, 128);
