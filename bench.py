@@ -234,6 +234,19 @@ def oracle_sample_run(wl, budget_s, steps, fill_budget=False):
     return mlups, sample, cores, dt
 
 
+def oracle_single_thread(workload, budget_s):
+    """The same oracle sample on one host thread, in a child process (OpenMP
+    reads its thread count when the library starts)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", workload,
+                              "--cpu-budget", str(budget_s)], env=env, capture_output=True, text=True,
+                             timeout=20 * budget_s + 120)
+        return json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][-1])
+    except Exception as e:  # report the failure instead of a number
+        return {"error": str(e)[:200]}
+
+
 def run_reference(args, world, rank):
     """The oracle arm: the FP64 CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -363,7 +376,8 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups, sample, cores, _ = oracle_sample_run(wl, args.cpu_budget, 4, fill_budget=True)
         line["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample,
+                                "single_thread": oracle_single_thread(args.workload, args.cpu_budget / 2)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -614,7 +628,13 @@ def main():
     ap.add_argument("--fp64-below", type=float, default=1e-6,
                     help="steady max|u| under which an FP32 domain is re-converged in FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample:  # child of oracle_single_thread: one sample, one JSON line
+        mlups, sample, cores, dt = oracle_sample_run(WORKLOADS[args.oracle_sample], args.cpu_budget, 2,
+                                                     fill_budget=True)
+        print(json.dumps({"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "sample": sample}))
+        return 0
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.sweep:
