@@ -16,6 +16,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <type_traits>
 
 #include "internal.h"
@@ -25,6 +28,25 @@ namespace lbm {
 
 constexpr double kPrA = 2.0 / 49.0;  // Peng-Robinson a, b (R = 1), Sec. 3
 constexpr double kPrB = 2.0 / 21.0;
+
+// Raises a kernel's dynamic shared-memory limit where it exceeds the 48 KB
+// default, once per (kernel, device): the attribute belongs to the device, and a
+// process may drive several.
+template <class K>
+cudaError_t ensure_dyn_smem(K kern, size_t dyn)
+{
+    if (dyn <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    if (cudaError_t e = cudaGetDevice(&dev); e != cudaSuccess) return e;
+    const std::pair<const void*, int> key(reinterpret_cast<const void*>(kern), dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(key)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
 
 // ---- small PTX helpers: shared-memory mbarrier and TMA ----------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -2180,15 +2202,7 @@ cudaError_t launch_onepass(const LaunchArgs& a, cudaStream_t s)
     constexpr int R = Stencil<Lattice<LAT>::D, ORD>::radius;
     constexpr size_t dyn = (ST == 2) ? sizeof(Real) * (R + 1) * Lattice<LAT>::Q * TX * TY : 0;
     auto kern = &k_onepass<LAT, ORD, COLL, Real, TX, TY, ZC, MINB, ST>;
-    if (dyn > 48 * 1024) {
-        static bool attr_set = false;  // per instantiation
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(dyn));
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
-    }
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     constexpr bool k3 = Lattice<LAT>::D == 3;
     const int ntx = (a.p.nx + TX - 1) / TX;
     const int nty = k3 ? (a.p.ny + TY - 1) / TY : 1;
@@ -2224,12 +2238,7 @@ cudaError_t launch_onepass_rowp2(const LaunchArgs& a, cudaStream_t s)
 {
     constexpr size_t dyn = sizeof(float) * NSTG * Lattice<LAT>::Q * (TY + 2) * NX;
     auto kern = &k_onepass_rowp2<LAT, ORD, NX, TY, NSTG>;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     if (a.p.nx != NX) return cudaErrorInvalidValue;
     const int nty = (a.p.ny + TY - 1) / TY;
     int dev = 0, nsm = 1;
@@ -2248,12 +2257,7 @@ cudaError_t launch_onepass_rowp(const LaunchArgs& a, cudaStream_t s)
 {
     constexpr size_t dyn = sizeof(Real) * NSTG * Lattice<LAT>::Q * (TY + 2) * NX;
     auto kern = &k_onepass_rowp<LAT, ORD, COLL, Real, NX, TY, NSTG>;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     if (a.p.nx != NX) return cudaErrorInvalidValue;
     const int nty = (a.p.ny + TY - 1) / TY;
     int dev = 0, nsm = 1;
@@ -2272,12 +2276,7 @@ cudaError_t launch_onepass_row(const LaunchArgs& a, cudaStream_t s)
 {
     constexpr size_t dyn = sizeof(Real) * NSTG * Lattice<LAT>::Q * (TY + 2) * NX;
     auto kern = &k_onepass_row<LAT, ORD, COLL, Real, NX, TY, ZC, NSTG, PROD>;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     if (a.p.nx != NX) return cudaErrorInvalidValue;
     const int nty = (a.p.ny + TY - 1) / TY;
     int zc = ZC;
@@ -2311,12 +2310,7 @@ cudaError_t launch_onepass_seg(const LaunchArgs& a, cudaStream_t s)
     constexpr int XP = 16 / static_cast<int>(sizeof(Real));
     constexpr size_t dyn = sizeof(Real) * NSTG * Lattice<LAT>::Q * (TX + 2 * XP);
     auto kern = &k_onepass_seg<LAT, ORD, COLL, Real, TX, ZC, NSTG>;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     if (a.p.nx % XP != 0) return cudaErrorInvalidValue;
     const int ntx = (a.p.nx + TX - 1) / TX;
     const long long nblocks = static_cast<long long>(ntx) * ((a.p.ny + ZC - 1) / ZC);
@@ -2335,12 +2329,7 @@ cudaError_t launch_onepass_async(const LaunchArgs& a, cudaStream_t s)
     constexpr int H = EX * EY - TX * TY;
     constexpr size_t dyn = sizeof(Real) * L::Q * ((R + 2) * TX * TY + 2 * H);
     auto kern = &k_onepass_async<LAT, ORD, COLL, Real, TX, TY, ZC, MINB>;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     constexpr bool k3 = L::D == 3;
     const int ntx = (a.p.nx + TX - 1) / TX;
     const int nty = k3 ? (a.p.ny + TY - 1) / TY : 1;
@@ -2358,15 +2347,7 @@ cudaError_t launch_onepass_la(const LaunchArgs& a, cudaStream_t s)
     constexpr int R = Stencil<L::D, ORD>::radius;
     constexpr size_t dyn = sizeof(Real) * (R + 2) * L::Q * TX * TY;
     auto kern = &k_onepass_la<LAT, ORD, COLL, Real, TX, TY, ZC, MINB, HL>;
-    if (dyn > 48 * 1024) {
-        static bool attr_set = false;  // per instantiation
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(dyn));
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
-    }
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     constexpr bool k3 = L::D == 3;
     const int ntx = (a.p.nx + TX - 1) / TX;
     const int nty = k3 ? (a.p.ny + TY - 1) / TY : 1;
@@ -2384,15 +2365,7 @@ cudaError_t launch_onepass_x2(const LaunchArgs& a, cudaStream_t s)
     constexpr int R = Stencil<L::D, ORD>::radius;
     constexpr size_t dyn = (ST == 2) ? sizeof(float2) * (R + 1) * L::Q * TX2 * TY : 0;
     auto kern = &k_onepass_x2<LAT, ORD, TX2, TY, ZC, MINB, ST>;
-    if (dyn > 48 * 1024) {
-        static bool attr_set = false;  // per instantiation
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(dyn));
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
-    }
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     constexpr bool k3 = L::D == 3;
     constexpr int TX = 2 * TX2;
     const int ntx = (a.p.nx + TX - 1) / TX;
