@@ -163,8 +163,10 @@ const char* lbm_step_kernel_name(const lbm_ctx* ctx, int i);
  * truncated to len).  With LBM_PATH_AUTO / LBM_PATH_ONE_PASS the first
  * lbm_step (or this call) times each compiled variant (tile shape, chunk
  * length, register cap; and the two-pass schedule under AUTO) on the current
- * state, without advancing it, and keeps the fastest.  The variants perform the
- * same arithmetic, so the choice changes speed only. */
+ * state, without advancing it, and keeps the fastest.  The variants compute the
+ * same step; FP64 and one-cell-per-thread FP32 variants are bitwise alike, while
+ * the packed-pair FP32 variants order their float operations differently and
+ * agree within FP32 round-off. */
 int lbm_schedule_report(lbm_ctx* ctx, char* buf, int len);
 
 /* Pins the step schedule to the named candidate (a name lbm_schedule_report
