@@ -18,11 +18,9 @@ import os
 
 import numpy as np
 import pytest
-from scipy.integrate import quad
-from scipy.optimize import brentq, fsolve
 
 import oracle
-from theory import mechanical_stability
+from theory import maxwell, mechanical_stability, pr_critical_T, pr_pressure
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -103,25 +101,14 @@ def test_peng_robinson_critical_point():
         assert np.sign(dpt.min()) == sign
 
 
-def maxwell(T_over_Tc):
-    """Equal-area coexistence of the oracle's P-R isotherm: p(rv) = p(rl) = p0,
-    int_{rv}^{rl} (p - p0) / rho^2 drho = 0."""
-    p = lambda r: oracle.pr_pressure(r, T_over_Tc)
-    rho = np.linspace(1e-3, 10.0, 40001)
-    pr = np.array([p(r) for r in rho])
-    dp = np.gradient(pr, rho)
-    spin = rho[np.where(np.diff(np.sign(dp)) != 0)[0]]
-    r_max, r_min = spin[0], spin[1]  # local max then local min of p
-
-    def area(p0):
-        rv = brentq(lambda r: p(r) - p0, 1e-12, r_max)
-        rl = brentq(lambda r: p(r) - p0, r_min, 9.9)
-        return quad(lambda r: (p(r) - p0) / r ** 2, rv, rl, limit=400)[0], rv, rl
-
-    lo, hi = max(p(r_min), p(1e-6)), p(r_max)
-    p0 = brentq(lambda q: area(q)[0], lo + 1e-14, hi - 1e-14, xtol=1e-15)
-    _, rv, rl = area(p0)
-    return rv, rl
+def test_peng_robinson_eos_matches_an_independent_form():
+    """The oracle's P-R EOS (Sec. 3: a = 2/49, b = 2/21, omega = 0.344) and its
+    critical temperature against the formula written out independently, with
+    T_c from exact symbolic derivatives."""
+    assert oracle.pr_critical_T() == pytest.approx(pr_critical_T(), rel=1e-12)
+    for T in (0.6, 0.75, 0.9, 0.95, 1.0):
+        for r in (0.01, 0.3, 1.0, 2.6, 5.0, 8.0):
+            assert oracle.pr_pressure(r, T) == pytest.approx(pr_pressure(r, T), rel=1e-11, abs=1e-15)
 
 
 def test_peng_robinson_density_ratio_range():
