@@ -37,7 +37,7 @@ _lib = None
 
 D2Q9, D3Q19, D2Q13, D2Q25 = 0, 1, 2, 3
 PSI_EXP, PSI_PR = 0, 1
-BGK, MRT = 0, 1
+BGK, MRT, EDM = 0, 1, 2
 
 _dptr = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _iptr = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")

@@ -15,7 +15,10 @@
  *   F(x)   = -G psi(x) sum_a w_a psi(x + e_a) e_a                        (Eq. 1)
  *   u(x)   = (sum_b f_b c_b + F/2) / rho          (Guo's half-force velocity, Eq. 4)
  *   f*_b   = f_b - (f_b - feq_b)/tau + phi_b                       (Eqs. 3-4, BGK)
- *            or the moment-space (MRT) collision with the same feq and phi
+ *            or the moment-space (MRT) collision with the same feq and phi,
+ *            or BGK with the exact-difference forcing the paper's runs use (Sec. 3):
+ *            f*_b = f_b - (f_b - feq_b(rho, u'))/tau + feq_b(rho, u' + F/rho) - feq_b(rho, u'),
+ *            u' = sum_b f_b c_b / rho (the physical velocity is still u' + F/(2 rho))
  *   f_b(x + c_b, n+1) = f*_b(x)                                    (Eq. 3, stream)
  *
  * Readings of the paper used here (each is also listed in the design notes):
@@ -42,7 +45,7 @@
 
 enum { OR_D2Q9 = 0, OR_D3Q19 = 1, OR_D2Q13 = 2, OR_D2Q25 = 3 };
 enum { OR_PSI_EXP = 0, OR_PSI_PR = 1 };
-enum { OR_BGK = 0, OR_MRT = 1 };
+enum { OR_BGK = 0, OR_MRT = 1, OR_EDM = 2 };
 
 /* ------------------------------------------------------------------------ */
 /* Shell tables: a velocity set or force stencil is every integer vector whose
@@ -352,6 +355,7 @@ or_sim* or_create(int lattice, int nx, int ny, int nz, int stencil_order, int ps
                   double s_e, double s_eps, double s_q)
 {
     if (lattice < 0 || lattice > 3 || nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5)) return NULL;
+    if (coll < OR_BGK || coll > OR_EDM) return NULL;
     or_sim* s = (or_sim*)calloc(1, sizeof(or_sim));
     s->lattice = lattice;
     shell_set ls = lattice_shells(lattice, &s->cs2);
@@ -536,6 +540,19 @@ void or_collide_cell(const or_sim* s, const double* fin, const double F[3], doub
         double pref = 1.0 - 1.0 / (2.0 * s->tau);
         for (int b = 0; b < s->Q; ++b)
             fout[b] = fin[b] - (fin[b] - feq[b]) / s->tau + pref * src[b];
+    } else if (s->coll == OR_EDM) {
+        /* exact difference: relax towards feq at the force-free velocity u', then
+         * add the change of feq that the velocity increment F/rho makes */
+        double up[3], uv[3];
+        for (int i = 0; i < 3; ++i) {
+            up[i] = j[i] / rho;
+            uv[i] = up[i] + F[i] / rho;
+        }
+        for (int b = 0; b < s->Q; ++b) {
+            double e0 = feq_b(s, b, rho, up);
+            double e1 = feq_b(s, b, rho, uv);
+            fout[b] = fin[b] - (fin[b] - e0) / s->tau + (e1 - e0);
+        }
     } else {
         double m[OR_MAXQ], meq[OR_MAXQ], ms[OR_MAXQ], mpost[OR_MAXQ];
         for (int k = 0; k < s->Q; ++k) {

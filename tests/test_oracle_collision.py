@@ -11,6 +11,10 @@
 - Streaming (Eq. 3) as the permutation f_b(x + c_b) <- f*_b(x), brute force.
 - MRT with every rate 1/tau is BGK; mass and momentum are conserved; a centred
   droplet stays mirror-symmetric.
+- Exact-difference forcing (the paper's runs, Sec. 3) through its moments: mass
+  kept, momentum gains exactly F, and the second moment is the BGK relaxation
+  towards feq at u' = j/rho plus rho (v v - u' u') with v = u' + F/rho; at
+  tau = 1 the result is the equilibrium at v.
 """
 import numpy as np
 import pytest
@@ -162,3 +166,42 @@ def test_centred_droplet_stays_symmetric():
     mirror_x = np.roll(rho[:, ::-1], 1, axis=1)  # x -> nx - x (mod nx)
     assert np.abs(rho - mirror_x).max() < 1e-12
     assert np.abs(rho - rho.T).max() < 1e-12
+
+
+@pytest.mark.parametrize("lat,order", LATS)
+@pytest.mark.parametrize("tau", [0.6, 1.0, 1.7])
+def test_exact_difference_forcing_moments(lat, order, tau):
+    rng = np.random.default_rng(13)
+    c, w, cs2 = lattice(lat)
+    dim = 3 if lat == oracle.D3Q19 else 2
+    sim = oracle.Sim(lat, 4, 4, 4 if dim == 3 else 1, stencil=order, tau=tau, coll=oracle.EDM)
+    iso = np.eye(3) * (np.abs(c).sum(0) > 0)
+    for _ in range(5):
+        fin = w * rng.uniform(0.5, 2.0, size=len(w))
+        F = np.zeros(3)
+        F[:dim] = rng.normal(scale=0.01, size=dim)
+        fout, rho, u = sim.collide_cell(fin, F)
+        j = fin @ c
+        up = j / rho
+        v = up + F / rho
+        np.testing.assert_allclose(u, (j + F / 2) / rho, rtol=1e-13, atol=1e-16)
+        assert fout.sum() == pytest.approx(fin.sum(), rel=1e-14)
+        np.testing.assert_allclose(fout @ c, j + F, atol=1e-14)
+        P_in = np.einsum("b,bi,bj->ij", fin, c, c)
+        P_eq = rho * cs2 * iso + rho * np.outer(up, up)
+        P_out = np.einsum("b,bi,bj->ij", fout, c, c)
+        expect = (1 - 1 / tau) * P_in + P_eq / tau + rho * (np.outer(v, v) - np.outer(up, up))
+        np.testing.assert_allclose(P_out, expect, atol=1e-13)
+        if tau == 1.0:
+            np.testing.assert_allclose(P_out, rho * cs2 * iso + rho * np.outer(v, v), atol=1e-13)
+
+
+def test_exact_difference_forcing_differs_from_guo():
+    """The two schemes share mass and momentum but not the second moment: at
+    tau = 0.6 with a finite force they must not coincide."""
+    c, w, cs2 = lattice(oracle.D2Q9)
+    fin = w * np.linspace(0.8, 1.2, len(w))
+    F = np.array([0.02, -0.01, 0.0])
+    a = oracle.Sim(oracle.D2Q9, 4, 4, tau=0.6, coll=oracle.EDM).collide_cell(fin, F)[0]
+    b = oracle.Sim(oracle.D2Q9, 4, 4, tau=0.6, coll=oracle.BGK).collide_cell(fin, F)[0]
+    assert np.abs(a - b).max() > 1e-6

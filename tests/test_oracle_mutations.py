@@ -25,6 +25,11 @@ MUTATIONS = [
      "tests/test_oracle_collision.py::test_mrt_with_uniform_rates_is_bgk"),
     ("half-force velocity", "u[i] = (j[i] + 0.5 * F[i]) / rho;", "u[i] = (j[i] + F[i]) / rho;",
      "tests/test_oracle_collision.py::test_guo_forcing_moments"),
+    ("exact-difference half increment", "uv[i] = up[i] + F[i] / rho;", "uv[i] = up[i] + 0.5 * F[i] / rho;",
+     "tests/test_oracle_collision.py::test_exact_difference_forcing_moments"),
+    ("exact-difference relaxes to the shifted state", "fout[b] = fin[b] - (fin[b] - e0) / s->tau + (e1 - e0);",
+     "fout[b] = fin[b] - (fin[b] - e1) / s->tau + (e1 - e0);",
+     "tests/test_oracle_collision.py::test_exact_difference_forcing_moments"),
 ]
 
 
