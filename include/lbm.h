@@ -64,7 +64,13 @@ typedef enum { LBM_STENCIL_LATTICE = 0, LBM_ISO4 = 4, LBM_ISO6 = 6, LBM_ISO8 = 8
  * omega = 0.344 and T = T_over_Tc * T_c (T_c the critical point of the EOS). */
 typedef enum { LBM_PSI_EXP = 0, LBM_PSI_PENG_ROBINSON = 1 } lbm_psi;
 
-typedef enum { LBM_BGK = 0, LBM_MRT = 1 } lbm_collision;
+/* LBM_BGK and LBM_MRT use Guo's forcing (Eq. 4).  LBM_BGK_EDM is BGK with the
+ * exact-difference forcing the paper's own runs use (Sec. 3):
+ *   f* = f - (f - feq(rho, u'))/tau + feq(rho, u' + F/rho) - feq(rho, u'),
+ *   u' = sum_b f_b c_b / rho; the reported velocity is u' + F/(2 rho) as with
+ *   Guo's scheme.  It is provided for the 2-D lattices (D2Q9, D2Q13, D2Q25);
+ *   other lattices return LBM_EUNSUPPORTED. */
+typedef enum { LBM_BGK = 0, LBM_MRT = 1, LBM_BGK_EDM = 2 } lbm_collision;
 
 /* Storage and arithmetic precision of the populations.  LBM_FP32_SHIFTED keeps
  * f - w_b rho_bar in float (rho_bar = mean density of the initial state);

@@ -403,7 +403,8 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     if (!(p->tau > 0.5)) return fail(LBM_EINVAL, "tau must exceed 1/2");
     if (!std::isfinite(p->G)) return fail(LBM_EINVAL, "G not finite");
     if (p->psi != LBM_PSI_EXP && p->psi != LBM_PSI_PENG_ROBINSON) return fail(LBM_EINVAL, "unknown psi");
-    if (p->collision != LBM_BGK && p->collision != LBM_MRT) return fail(LBM_EINVAL, "unknown collision");
+    if (p->collision != LBM_BGK && p->collision != LBM_MRT && p->collision != LBM_BGK_EDM)
+        return fail(LBM_EINVAL, "unknown collision");
     if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED) return fail(LBM_EINVAL, "unknown precision");
     if (p->path < LBM_PATH_AUTO || p->path > LBM_PATH_ONE_PASS) return fail(LBM_EINVAL, "unknown path");
     int order = p->stencil == LBM_STENCIL_LATTICE ? li.iso_order : p->stencil;
@@ -412,6 +413,8 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     if (g < 0) return fail(LBM_EUNSUPPORTED, "no %d-D stencil of order %d", li.D, order);
     if (p->collision == LBM_MRT && !(p->lattice == LBM_D2Q9 || p->lattice == LBM_D3Q19))
         return fail(LBM_EUNSUPPORTED, "MRT is provided for D2Q9 and D3Q19 only");
+    if (p->collision == LBM_BGK_EDM && li.D != 2)
+        return fail(LBM_EUNSUPPORTED, "exact-difference forcing is provided for the 2-D lattices");
     if (p->collision == LBM_MRT) {
         const double r[3] = {p->s_e, p->s_eps, p->s_q};
         for (double v : r)

@@ -297,7 +297,7 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
             f[b] = f[b] * om1 + Real(wb) * (ev + cP);
             f[b + 1] = f[b + 1] * om1 + Real(wb) * (ev - cP);
         });
-    } else {
+    } else if constexpr (COLL == 1) {
         // Moment space: f* = f + M^-1 [ -S (m - m_eq) + (I - S/2) M phi~ ],
         // m_eq := M feq, M^-1 = M^T diag(1/|row|^2) (orthogonal rows).
         using MB = Mrt<LAT>;
@@ -341,6 +341,39 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
             });
             f[b] = f[b] + acc;
         });
+    } else {
+        // Exact-difference forcing with BGK (the scheme of the paper's runs, Sec. 3):
+        //   f* = feq(rho, v) + (1 - omega) (f - feq(rho, u')),  u' = j / rho, v = u' + F / rho,
+        // regrouped as w_b [ A0 + q_b +- c.P ] with
+        //   A0 = omega rho - rho (v.v - (1 - omega) u'.u') / (2 cs2)   (FP32: omega (rho - rho_bar)),
+        //   P  = rho (v - (1 - omega) u') / cs2,
+        //   q_b = rho ((c.v)^2 - (1 - omega) (c.u')^2) / (2 cs4)   (even under c -> -c).
+        const Real upx = jx * inv_rho, upy = jy * inv_rho, upz = jz * inv_rho;
+        const Real vx = (jx + F[0]) * inv_rho, vy = (jy + F[1]) * inv_rho, vz = (jz + F[2]) * inv_rho;
+        const Real om1 = Real(1) - omega;
+        const Real vv = vx * vx + vy * vy + vz * vz;
+        const Real uu = upx * upx + upy * upy + upz * upz;
+        const Real A0 = (kDev ? omega * s : omega * rho) - rho * (vv - om1 * uu) * Real(0.5 / cs2);
+        const Real Px = rho * (vx - om1 * upx) * inv_cs2;
+        const Real Py = rho * (vy - om1 * upy) * inv_cs2;
+        const Real Pz = rho * (vz - om1 * upz) * inv_cs2;
+        const Real hq = rho * half_inv_cs4;
+        {
+            constexpr double w0 = L::T.w[0];
+            f[0] = f[0] * om1 + Real(w0) * A0;
+        }
+        sfor<(L::Q - 1) / 2>([&](auto kI) {
+            constexpr int b = 1 + 2 * decltype(kI)::value;
+            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
+            constexpr double wb = L::T.w[b];
+            const Real cv = Real(cx) * vx + Real(cy) * vy + Real(cz) * vz;
+            const Real cu = Real(cx) * upx + Real(cy) * upy + Real(cz) * upz;
+            const Real cP = Real(cx) * Px + Real(cy) * Py + Real(cz) * Pz;
+            const Real ev = A0 + hq * (cv * cv - om1 * cu * cu);
+            f[b] = f[b] * om1 + Real(wb) * (ev + cP);
+            f[b + 1] = f[b + 1] * om1 + Real(wb) * (ev - cP);
+        });
+        (void)ux; (void)uy; (void)uz; (void)usq; (void)uF; (void)pref;
     }
 }
 

@@ -37,6 +37,22 @@ bool kernels_d2q9(int order, int coll, int fp32, KernelSet* ks)
         *ks = fp32 ? make_set<kLatD2Q9, 10, 1, float>() : make_set<kLatD2Q9, 10, 1, double>();
         return true;
     }
+    if (order == 4 && coll == 2) {
+        *ks = fp32 ? make_set<kLatD2Q9, 4, 2, float>() : make_set<kLatD2Q9, 4, 2, double>();
+        return true;
+    }
+    if (order == 6 && coll == 2) {
+        *ks = fp32 ? make_set<kLatD2Q9, 6, 2, float>() : make_set<kLatD2Q9, 6, 2, double>();
+        return true;
+    }
+    if (order == 8 && coll == 2) {
+        *ks = fp32 ? make_set<kLatD2Q9, 8, 2, float>() : make_set<kLatD2Q9, 8, 2, double>();
+        return true;
+    }
+    if (order == 10 && coll == 2) {
+        *ks = fp32 ? make_set<kLatD2Q9, 10, 2, float>() : make_set<kLatD2Q9, 10, 2, double>();
+        return true;
+    }
     return false;
 }
 

@@ -5,10 +5,11 @@ consistent D2Q13 / D2Q25 models (lattice = force stencil), at the paper's
 equal-viscosity relaxation times (tau = 1, 11/12, 19/24).  Each run goes to
 steady state; the line reports max|u|, the coexistence densities and steps.
 
-    python -m paper_1906_11027_gb300.experiments [--temps 0.6,0.7,0.8,0.9,0.95]
+    python -m paper_1906_11027_gb300.experiments [--temps 0.6,0.7,0.8,0.9,0.95] [--forcing edm]
 
-The forcing is Guo's (the paper's own runs use the exact-difference method),
-so the numbers show the trend, not the paper's curves.
+--forcing guo (the default) uses Guo's scheme with BGK; --forcing edm uses the
+exact-difference method the paper's own runs use.  The figures' data are not
+available, so the numbers show the trend, not the paper's curves.
 """
 from __future__ import annotations
 
@@ -77,6 +78,7 @@ def main():
     ap.add_argument("--n", type=int, default=60)
     ap.add_argument("--r0", type=float, default=15.0)
     ap.add_argument("--max-steps", type=int, default=200000)
+    ap.add_argument("--forcing", choices=["guo", "edm"], default="guo")
     a = ap.parse_args()
     lbm.load()
     Tc = critical_T()
@@ -84,17 +86,18 @@ def main():
     for T in [float(t) for t in a.temps.split(",")]:
         rv, rl = maxwell(T, Tc)
         for name, lat, st, tau in MODELS:
+            coll = lbm.LBM_BGK_EDM if a.forcing == "edm" else lbm.LBM_BGK
             dom = lbm.Domain(a.n, a.n, lattice=lat, stencil=st, psi=lbm.LBM_PSI_PENG_ROBINSON, T_over_Tc=T,
-                             G=-1.0, tau=tau)
+                             G=-1.0, tau=tau, collision=coll)
             dom.init_droplet(rl, rv, a.r0, 3.0)
             try:
                 steps, ok = dom.run_to_steady(1e-10, a.max_steps, 100)
                 o = dom.observables()
-                row = dict(T_over_Tc=T, model=name, tau=round(tau, 4), steps=steps, steady=ok,
+                row = dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), steps=steps, steady=ok,
                            max_u=o["max_u"], mean_u=o["mean_u"], rho_l=o["rho_l"], rho_v=o["rho_g"],
                            maxwell_rho_l=rl, maxwell_rho_v=rv)
             except lbm.LbmError as e:
-                row = dict(T_over_Tc=T, model=name, tau=round(tau, 4), error=str(e))
+                row = dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), error=str(e))
             dom.close()
             rows.append(row)
             print(json.dumps(row), flush=True)

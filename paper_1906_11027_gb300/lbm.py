@@ -19,7 +19,7 @@ LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ENOTCONVERGED, LBM_EIO = -4, -5, -6
 LBM_D2Q9, LBM_D3Q19, LBM_D2Q13, LBM_D2Q25 = 0, 1, 2, 3
 LBM_STENCIL_LATTICE, LBM_ISO4, LBM_ISO6, LBM_ISO8, LBM_ISO10 = 0, 4, 6, 8, 10
 LBM_PSI_EXP, LBM_PSI_PENG_ROBINSON = 0, 1
-LBM_BGK, LBM_MRT = 0, 1
+LBM_BGK, LBM_MRT, LBM_BGK_EDM = 0, 1, 2
 LBM_FP64, LBM_FP32_SHIFTED = 0, 1
 LBM_PATH_AUTO, LBM_PATH_TWO_PASS, LBM_PATH_ONE_PASS = 0, 1, 2
 

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.test_oracle_physics import maxwell
+from theory import maxwell
 
 pytestmark = pytest.mark.gpu
 
@@ -82,6 +82,47 @@ def test_2d_ragged_domain_matches_oracle(lbm, lattice, stencil, coll):
         d.init_droplet(1.9, 0.15, 8.0, 2.0)
     dom.step(150)
     ref.step(150)
+    assert rel_max(dom.get_f(), ref.get_f()) <= 1e-12
+
+
+@pytest.mark.parametrize("lattice,stencil", [(0, 4), (0, 8), (0, 10), (2, 0), (3, 0)])
+def test_exact_difference_forcing_matches_oracle(lbm, lattice, stencil):
+    """BGK with the exact-difference forcing of the paper's runs, FP64, on the
+    ragged 37 x 29 box, against the oracle to 1e-12."""
+    tau = {0: 0.8, 2: 11 / 12, 3: 19 / 24}[lattice]
+    dom, ref = pair(lbm, lattice, (1, 29, 37), stencil=stencil, coll=lbm.LBM_BGK_EDM, tau=tau)
+    for d in (dom, ref):
+        d.init_droplet(1.9, 0.15, 8.0, 2.0)
+    dom.step(150)
+    ref.step(150)
+    assert rel_max(dom.get_f(), ref.get_f()) <= 1e-12
+    assert dom.observables()["max_u"] == pytest.approx(ref.observables()["max_u"], rel=1e-9)
+
+
+def test_exact_difference_forcing_fp32_and_3d(lbm):
+    """FP32 deviation storage with the exact-difference forcing stays within the
+    FP32 budget of the oracle; a 3-D lattice is refused."""
+    dom, ref = pair(lbm, lbm.LBM_D2Q9, (1, 64, 64), stencil=4, coll=lbm.LBM_BGK_EDM, precision=1)
+    for d in (dom, ref):
+        d.init_droplet(2.0, 0.15, 16.0, 2.0)
+    dom.step(300)
+    ref.step(300)
+    assert rel_max(dom.get_f(), ref.get_f()) <= 2e-4
+    with pytest.raises(lbm.LbmError):
+        lbm.Domain(16, 16, 16, lattice=lbm.LBM_D3Q19, collision=lbm.LBM_BGK_EDM)
+
+
+@pytest.mark.parametrize("T_over_Tc", [0.9, 0.8])
+def test_peng_robinson_exact_difference_matches_oracle(lbm, T_over_Tc):
+    """The paper's configuration: P-R psi with the exact-difference forcing,
+    on D2Q25 (lattice as stencil) at T/Tc = 0.9 and 0.8."""
+    rv, rl = maxwell(T_over_Tc)
+    dom, ref = pair(lbm, lbm.LBM_D2Q25, (1, 40, 40), stencil=0, psi=1, T_over_Tc=T_over_Tc, G=-1.0,
+                    tau=19 / 24, coll=lbm.LBM_BGK_EDM)
+    for d in (dom, ref):
+        d.init_droplet(rl, rv, 10.0, 3.0)
+    dom.step(200)
+    ref.step(200)
     assert rel_max(dom.get_f(), ref.get_f()) <= 1e-12
 
 
