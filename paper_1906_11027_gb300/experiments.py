@@ -1,11 +1,21 @@
-"""Spurious currents against temperature, the comparison of the paper's Sec. 3
-(Figs. 2-3): a static Peng-Robinson droplet on a 60 x 60 periodic box,
-r0 = 15, for D2Q9 with force stencils of 4th/6th/8th-order isotropy and for the
-consistent D2Q13 / D2Q25 models (lattice = force stencil), at the paper's
-equal-viscosity relaxation times (tau = 1, 11/12, 19/24).  Each run goes to
-steady state; the line reports max|u|, the coexistence densities and steps.
+"""The temperature sweeps of the paper's Sec. 3, for D2Q9 with force stencils
+of 4th/6th/8th-order isotropy and for the consistent D2Q13 / D2Q25 models
+(lattice = force stencil).  D2Q13 and D2Q25 run at tau = 1 ("T") and at the
+equal-viscosity tau = 11/12 and 19/24 ("V"), as in Fig. 3.
 
-    python -m paper_1906_11027_gb300.experiments [--temps 0.6,0.7,0.8,0.9,0.95] [--forcing edm]
+--case droplet (Figs. 2-3): a static Peng-Robinson droplet on a 60 x 60
+periodic box, r0 = 15, run to steady state and then --extra steps
+further (the line gives the relative drift over those); it reports max|u| and
+mean|u| (the spurious currents) with the centre and far-corner densities.
+
+--case flat (Figs. 4-5): a liquid slab between two flat interfaces normal to x
+on a periodic 200 x 8 strip, started from the Maxwell densities; the line
+reports the coexistence densities against the Maxwell construction and the
+interface thickness, i.e. the width of the region 1.05 rho_v <= rho <=
+0.95 rho_l with the run's own bulk densities: the node count per interface and
+the distance between the linearly interpolated crossings of the two levels.
+
+    python -m paper_1906_11027_gb300.experiments [--case flat] [--forcing edm] [--temps 0.7,0.8,0.9]
 
 --forcing guo (the default) uses Guo's scheme with BGK; --forcing edm uses the
 exact-difference method the paper's own runs use.  The figures' data are not
@@ -27,8 +37,9 @@ from paper_1906_11027_gb300 import lbm  # noqa: E402
 # Peng-Robinson of Sec. 3: a = 2/49, b = 2/21, R = 1, omega = 0.344
 A, B, OMEGA = 2.0 / 49.0, 2.0 / 21.0, 0.344
 MODELS = (("D2Q9 E4", lbm.LBM_D2Q9, 4, 1.0), ("D2Q9 E6", lbm.LBM_D2Q9, 6, 1.0),
-          ("D2Q9 E8", lbm.LBM_D2Q9, 8, 1.0), ("D2Q13", lbm.LBM_D2Q13, 0, 11.0 / 12.0),
-          ("D2Q25", lbm.LBM_D2Q25, 0, 19.0 / 24.0))
+          ("D2Q9 E8", lbm.LBM_D2Q9, 8, 1.0), ("D2Q13T", lbm.LBM_D2Q13, 0, 1.0),
+          ("D2Q13V", lbm.LBM_D2Q13, 0, 11.0 / 12.0), ("D2Q25T", lbm.LBM_D2Q25, 0, 1.0),
+          ("D2Q25V", lbm.LBM_D2Q25, 0, 19.0 / 24.0))
 
 
 def _p(rho, T, alpha):
@@ -72,6 +83,67 @@ def maxwell(T_over_Tc, Tc):
     return rv, rl
 
 
+def interface_thickness(line, rho_v, rho_l):
+    """Width of the rising interface of a periodic line profile (vapour at the
+    ends, liquid in the middle) between the levels 1.05 rho_v and 0.95 rho_l:
+    (nodes inside the band on each of the two interfaces, the mean of both, and
+    the mean distance between the interpolated level crossings)."""
+    lo, hi = 1.05 * rho_v, 0.95 * rho_l
+    n = len(line)
+    half = n // 2
+    inside = (line >= lo) & (line <= hi)
+    counts = (int(inside[:half].sum()), int(inside[half:].sum()))
+
+    def crossing(seg, level):
+        # first index i with seg[i] < level <= seg[i+1], interpolated linearly
+        for i in range(len(seg) - 1):
+            if seg[i] < level <= seg[i + 1]:
+                return i + (level - seg[i]) / (seg[i + 1] - seg[i])
+        return float("nan")
+    rise = line[:half + 1]
+    fall = line[half:][::-1]  # the falling interface read from the far side
+    widths = [crossing(seg, hi) - crossing(seg, lo) for seg in (rise, fall)]
+    return counts, float(np.mean(widths))
+
+
+def run_droplet(a, T, Tc, rv, rl, name, lat, st, tau, coll):
+    dom = lbm.Domain(a.n, a.n, lattice=lat, stencil=st, psi=lbm.LBM_PSI_PENG_ROBINSON, T_over_Tc=T,
+                     G=-1.0, tau=tau, collision=coll)
+    try:
+        dom.init_droplet(rl, rv, a.r0, 3.0)
+        steps, ok = dom.run_to_steady(1e-10, a.max_steps, 100)
+        o1 = dom.observables()
+        dom.step(a.extra)
+        o = dom.observables()
+        return dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), steps=steps, steady=ok,
+                    max_u=o["max_u"], mean_u=o["mean_u"], rho_l=o["rho_l"], rho_v=o["rho_g"],
+                    maxwell_rho_l=rl, maxwell_rho_v=rv, extra_steps=a.extra,
+                    max_u_drift=abs(o["max_u"] / o1["max_u"] - 1.0))
+    finally:
+        dom.close()
+
+
+def run_flat(a, T, Tc, rv, rl, name, lat, st, tau, coll):
+    dom = lbm.Domain(a.flat_nx, 8, lattice=lat, stencil=st, psi=lbm.LBM_PSI_PENG_ROBINSON, T_over_Tc=T,
+                     G=-1.0, tau=tau, collision=coll)
+    try:
+        dom.init_flat(rl, rv, 3.0, 0)
+        steps, ok = dom.run_to_steady(1e-10, a.max_steps, 100)
+        rho_v1 = dom.observables()["rho_g"]
+        dom.step(a.extra)
+        o = dom.observables()
+        line = dom.fields()["rho"][0, 4, :]
+        rho_l, rho_v = float(line[a.flat_nx // 2]), float(line[0])
+        counts, width = interface_thickness(line, rho_v, rho_l)
+        return dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), steps=steps, steady=ok,
+                    rho_l=rho_l, rho_v=rho_v, maxwell_rho_l=rl, maxwell_rho_v=rv,
+                    rho_l_rel_dev=rho_l / rl - 1.0, rho_v_rel_dev=rho_v / rv - 1.0,
+                    thickness_nodes=counts, thickness=width, max_u=o["max_u"], extra_steps=a.extra,
+                    rho_v_drift=abs(rho_v / rho_v1 - 1.0))
+    finally:
+        dom.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--temps", default="0.6,0.7,0.8,0.85,0.9,0.95")
@@ -79,26 +151,26 @@ def main():
     ap.add_argument("--r0", type=float, default=15.0)
     ap.add_argument("--max-steps", type=int, default=200000)
     ap.add_argument("--forcing", choices=["guo", "edm"], default="guo")
+    ap.add_argument("--case", choices=["droplet", "flat"], default="droplet")
+    ap.add_argument("--flat-nx", type=int, default=200)
+    ap.add_argument("--extra", type=int, default=20000,
+                    help="steps run after the steady test passes; the values reported are taken after them, "
+                         "with their drift over those steps")
+    ap.add_argument("--models", default="", help="comma-separated subset of: " + ", ".join(m[0] for m in MODELS))
     a = ap.parse_args()
+    models = [m for m in MODELS if not a.models or m[0] in a.models.split(",")]
+    run = run_flat if a.case == "flat" else run_droplet
+    coll = lbm.LBM_BGK_EDM if a.forcing == "edm" else lbm.LBM_BGK
     lbm.load()
     Tc = critical_T()
     rows = []
     for T in [float(t) for t in a.temps.split(",")]:
         rv, rl = maxwell(T, Tc)
-        for name, lat, st, tau in MODELS:
-            coll = lbm.LBM_BGK_EDM if a.forcing == "edm" else lbm.LBM_BGK
-            dom = lbm.Domain(a.n, a.n, lattice=lat, stencil=st, psi=lbm.LBM_PSI_PENG_ROBINSON, T_over_Tc=T,
-                             G=-1.0, tau=tau, collision=coll)
-            dom.init_droplet(rl, rv, a.r0, 3.0)
+        for name, lat, st, tau in models:
             try:
-                steps, ok = dom.run_to_steady(1e-10, a.max_steps, 100)
-                o = dom.observables()
-                row = dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), steps=steps, steady=ok,
-                           max_u=o["max_u"], mean_u=o["mean_u"], rho_l=o["rho_l"], rho_v=o["rho_g"],
-                           maxwell_rho_l=rl, maxwell_rho_v=rv)
+                row = run(a, T, Tc, rv, rl, name, lat, st, tau, coll)
             except lbm.LbmError as e:
-                row = dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), error=str(e))
-            dom.close()
+                row = dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), case=a.case, error=str(e))
             rows.append(row)
             print(json.dumps(row), flush=True)
     return 0
