@@ -15,6 +15,8 @@ and plane-wave Taylor series of the force (Eqs. 1-2), the closed-form one-step
 update at u = 0 and tau = 1 (Eqs. 5-6), moments of feq and of Guo's source
 (Eq. 4), streaming as a permutation (Eq. 3), MRT = BGK at uniform rates,
 shear-wave viscosity c_s^2 (tau - 1/2) (Sec. 3, tau = 11/12 and 19/24),
+the wall of Fig. 6 (the one-sided force of a virtual wall density in closed
+form, no-slip shear-wave decay in a bounce-back channel),
 conservation of mass and momentum, the Peng-Robinson critical point and
 density-ratio range (Sec. 3), flat-interface coexistence from mechanical
 stability and Laplace's law.
@@ -89,6 +91,7 @@ def _load():
             "or_pr_critical_T": (D, []),
             "or_pr_alpha": (D, [D]),
             "or_pr_pressure": (D, [D, D, D]),
+            "or_set_wall": (I, [P, I, D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -160,6 +163,12 @@ class Sim:
         if h:
             self._lib.or_destroy(h)
             self._h = None
+
+    def set_wall(self, rows, rho_w):
+        """Solid band y < rows with virtual wall density rho_w (Sec. 3, Fig. 6)."""
+        if not self._lib.or_set_wall(self._h, int(rows), float(rho_w)):
+            raise ValueError("oracle: wall band thinner than the lattice reach or force radius, or bad rho_w")
+        self.wall_rows = int(rows)
 
     # -- initial conditions
     def init_droplet(self, rho_l, rho_g, R, width):

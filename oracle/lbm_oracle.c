@@ -21,6 +21,11 @@
  *            u' = sum_b f_b c_b / rho (the physical velocity is still u' + F/(2 rho))
  *   f_b(x + c_b, n+1) = f*_b(x)                                    (Eq. 3, stream)
  *
+ * Optional wall (Sec. 3, Fig. 6; or_set_wall): the rows y < wall_rows are solid.
+ * A solid node takes no collision; it sends every population back the way it
+ * came, f*_b = f_{-b} (standard, full-way bounce-back), and in Eq. 1 it carries
+ * psi(rho_w), the wall's virtual density, which sets the wettability.
+ *
  * Readings of the paper used here (each is also listed in the design notes):
  *  - Force weights w_a are stored unit-normalised (sum_a w_a e_ax^2 = 1) and are
  *    multiplied by the lattice's c_s^2, so c_s'^2 = c_s^2 on every lattice and
@@ -262,6 +267,9 @@ typedef struct {
     double M[OR_MAXQ][OR_MAXQ], Minv[OR_MAXQ][OR_MAXQ];
     double *f, *ftmp, *rho, *psi;
     int64_t step;
+    int wall_rows;          /* rows y < wall_rows are solid; 0 = no wall */
+    double rho_w, psi_w;    /* the wall's virtual density and its psi */
+    int opp[OR_MAXQ];       /* c_opp[b] = -c_b */
 } or_sim;
 
 /* ---- moment basis for MRT --------------------------------------------- */
@@ -573,6 +581,8 @@ void or_collide_cell(const or_sim* s, const double* fin, const double F[3], doub
     if (u_out) for (int i = 0; i < 3; ++i) u_out[i] = u[i];
 }
 
+static int is_solid(const or_sim* s, int y) { return y < s->wall_rows; }
+
 static void update_rho_psi(or_sim* s)
 {
     #pragma omp parallel for schedule(static)
@@ -580,8 +590,37 @@ static void update_rho_psi(or_sim* s)
         double r = 0.0;
         for (int b = 0; b < s->Q; ++b) r += s->f[(size_t)b * s->N + n];
         s->rho[n] = r;
-        s->psi[n] = or_psi_of_rho(s, r);
+        s->psi[n] = is_solid(s, (n / s->nx) % s->ny) ? s->psi_w : or_psi_of_rho(s, r);
     }
+}
+
+/* Solid band y < rows with virtual wall density rho_w (Sec. 3, Fig. 6).  The
+ * box stays periodic in y, so the band is the floor of the fluid and the
+ * ceiling of its periodic image: it must be at least as thick as the lattice's
+ * reach and the force stencil's radius so that no population and no term of
+ * Eq. 1 crosses it, and it must leave fluid rows.  Returns 1, or 0 (nothing
+ * changed) for a band that breaks these rules or a psi(rho_w) that is not
+ * finite. */
+int or_set_wall(or_sim* s, int rows, double rho_w)
+{
+    int reach = 0, radius = 0;
+    for (int b = 0; b < s->Q; ++b)
+        for (int i = 0; i < 3; ++i) reach = abs(s->c[b][i]) > reach ? abs(s->c[b][i]) : reach;
+    for (int a = 0; a < s->ne; ++a)
+        for (int i = 0; i < 3; ++i) radius = abs(s->e[a][i]) > radius ? abs(s->e[a][i]) : radius;
+    if (rows != 0 && (rows < reach || rows < radius || rows >= s->ny)) return 0;
+    double pw = or_psi_of_rho(s, rho_w);
+    if (rows != 0 && !isfinite(pw)) return 0;
+    for (int b = 0; b < s->Q; ++b) {
+        s->opp[b] = -1;
+        for (int k = 0; k < s->Q; ++k)
+            if (s->c[k][0] == -s->c[b][0] && s->c[k][1] == -s->c[b][1] && s->c[k][2] == -s->c[b][2]) s->opp[b] = k;
+        if (s->opp[b] < 0) return 0;
+    }
+    s->wall_rows = rows;
+    s->rho_w = rho_w;
+    s->psi_w = pw;
+    return 1;
 }
 
 /* n time steps. */
@@ -596,8 +635,12 @@ void or_step(or_sim* s, int64_t nsteps)
                     size_t n = cell_index(s, x, y, z);
                     double fin[OR_MAXQ], fout[OR_MAXQ], F[3];
                     for (int b = 0; b < s->Q; ++b) fin[b] = s->f[(size_t)b * s->N + n];
-                    force_at(s, s->psi, x, y, z, F);
-                    or_collide_cell(s, fin, F, fout, NULL, NULL);
+                    if (is_solid(s, y)) {
+                        for (int b = 0; b < s->Q; ++b) fout[b] = fin[s->opp[b]];
+                    } else {
+                        force_at(s, s->psi, x, y, z, F);
+                        or_collide_cell(s, fin, F, fout, NULL, NULL);
+                    }
                     for (int b = 0; b < s->Q; ++b) {
                         size_t dst = cell_index(s, wrap(x + s->c[b][0], s->nx),
                                                wrap(y + s->c[b][1], s->ny),
@@ -671,7 +714,8 @@ void or_get_f(const or_sim* s, double* f) { memcpy(f, s->f, sizeof(double) * (si
 /* ---- macroscopic fields and observables -------------------------------- */
 
 /* rho, psi, F (3 per cell) and u (3 per cell) of the current state; any output
- * may be NULL. */
+ * may be NULL.  Solid nodes report F = u = 0 (rho is the sum of the populations
+ * they hold, psi the wall's). */
 void or_fields(or_sim* s, double* rho, double* psi, double* F, double* u)
 {
     update_rho_psi(s);
@@ -680,14 +724,15 @@ void or_fields(or_sim* s, double* rho, double* psi, double* F, double* u)
             for (int x = 0; x < s->nx; ++x) {
                 size_t n = cell_index(s, x, y, z);
                 double Fl[3], j[3] = { 0.0, 0.0, 0.0 };
+                const int solid = is_solid(s, y);
                 force_at(s, s->psi, x, y, z, Fl);
                 for (int b = 0; b < s->Q; ++b)
                     for (int i = 0; i < 3; ++i) j[i] += s->f[(size_t)b * s->N + n] * s->c[b][i];
                 if (rho) rho[n] = s->rho[n];
                 if (psi) psi[n] = s->psi[n];
                 for (int i = 0; i < 3; ++i) {
-                    if (F) F[3 * n + i] = Fl[i];
-                    if (u) u[3 * n + i] = (j[i] + 0.5 * Fl[i]) / s->rho[n];
+                    if (F) F[3 * n + i] = solid ? 0.0 : Fl[i];
+                    if (u) u[3 * n + i] = solid ? 0.0 : (j[i] + 0.5 * Fl[i]) / s->rho[n];
                 }
             }
 }
@@ -695,14 +740,21 @@ void or_fields(or_sim* s, double* rho, double* psi, double* F, double* u)
 /* out[0..10] = rho_l (centre node), rho_g (node 0), dp = p(rho_l) - p(rho_g),
  * max|u|, mean|u|, mass, momentum x, y, z (sum of rho u), thickness (number
  * of nodes along the x line through the centre with 1.05 rho_g <= rho <=
- * 0.95 rho_l; meaningful for flat interfaces), step. */
+ * 0.95 rho_l; meaningful for flat interfaces), step.
+ * With a wall: rho_l is read at (nx/2, wall_rows, nz/2), the first fluid node
+ * above the wall under the centre, rho_g at (0, ny - 1, 0), the top fluid row;
+ * max|u|, mean|u| and the momentum run over fluid nodes only (the mean divides
+ * by their number); mass still sums every node, which the scheme conserves. */
 void or_observables(or_sim* s, double* out)
 {
     double* u = (double*)malloc(sizeof(double) * 3 * s->N);
     or_fields(s, NULL, NULL, NULL, u);
     double mass = 0.0, mom[3] = { 0.0, 0.0, 0.0 }, umax = 0.0, usum = 0.0;
+    int nfluid = 0;
     for (int n = 0; n < s->N; ++n) {
         mass += s->rho[n];
+        if (is_solid(s, (n / s->nx) % s->ny)) continue;
+        nfluid += 1;
         double m2 = 0.0;
         for (int i = 0; i < 3; ++i) {
             mom[i] += s->rho[n] * u[3 * n + i];
@@ -712,8 +764,9 @@ void or_observables(or_sim* s, double* out)
         usum += um;
         if (um > umax) umax = um;
     }
-    size_t centre = cell_index(s, s->nx / 2, s->ny / 2, s->nz / 2);
-    double rl = s->rho[centre], rg = s->rho[0];
+    size_t centre = cell_index(s, s->nx / 2, s->wall_rows ? s->wall_rows : s->ny / 2, s->nz / 2);
+    size_t far = s->wall_rows ? cell_index(s, 0, s->ny - 1, 0) : 0;
+    double rl = s->rho[centre], rg = s->rho[far];
     double thick = 0.0;
     for (int x = 0; x < s->nx; ++x) {
         double r = s->rho[cell_index(s, x, s->ny / 2, s->nz / 2)];
@@ -723,7 +776,7 @@ void or_observables(or_sim* s, double* out)
     out[1] = rg;
     out[2] = or_pressure(s, rl) - or_pressure(s, rg);
     out[3] = umax;
-    out[4] = usum / s->N;
+    out[4] = usum / nfluid;
     out[5] = mass;
     out[6] = mom[0]; out[7] = mom[1]; out[8] = mom[2];
     out[9] = thick;

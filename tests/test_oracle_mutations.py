@@ -30,6 +30,19 @@ MUTATIONS = [
     ("exact-difference relaxes to the shifted state", "fout[b] = fin[b] - (fin[b] - e0) / s->tau + (e1 - e0);",
      "fout[b] = fin[b] - (fin[b] - e1) / s->tau + (e1 - e0);",
      "tests/test_oracle_collision.py::test_exact_difference_forcing_moments"),
+    ("wall passes populations through", "for (int b = 0; b < s->Q; ++b) fout[b] = fin[s->opp[b]];",
+     "for (int b = 0; b < s->Q; ++b) fout[b] = fin[b];",
+     "tests/test_oracle_wall.py::test_wall_channel_shear_wave_decays_with_no_slip"),
+    ("wall reflects specularly", "if (s->c[k][0] == -s->c[b][0] && s->c[k][1] == -s->c[b][1]",
+     "if (s->c[k][0] == s->c[b][0] && s->c[k][1] == -s->c[b][1]",
+     "tests/test_oracle_wall.py::test_wall_channel_shear_wave_decays_with_no_slip"),
+    ("wall psi from the populations it holds",
+     "s->psi[n] = is_solid(s, (n / s->nx) % s->ny) ? s->psi_w : or_psi_of_rho(s, r);",
+     "s->psi[n] = or_psi_of_rho(s, r);",
+     "tests/test_oracle_wall.py::test_wall_force_is_one_sided"),
+    ("wall one row too thick", "static int is_solid(const or_sim* s, int y) { return y < s->wall_rows; }",
+     "static int is_solid(const or_sim* s, int y) { return y <= s->wall_rows; }",
+     "tests/test_oracle_wall.py::test_wall_force_is_one_sided"),
 ]
 
 
