@@ -104,10 +104,25 @@ typedef struct lbm_params {
     void* (*dev_alloc)(size_t bytes, void* alloc_ctx);  /* NULL: cudaMalloc */
     void (*dev_free)(void* ptr, void* alloc_ctx);
     void* alloc_ctx;
+    /* Wall (Sec. 3, Fig. 6), 2-D lattices, two-pass schedule: the rows
+     * y < wall_rows are solid.  A solid node takes no collision and returns every
+     * population the way it came, f*_b = f_{-b} (standard bounce-back); in Eq. 1
+     * it carries psi(rho_w), the virtual wall density that sets the
+     * wettability.  The box stays periodic, so the band is the floor of the fluid
+     * and its ceiling; wall_rows must be at least the lattice's reach and the
+     * force stencil's radius (LBM_EINVAL otherwise), and psi(rho_w) must exist
+     * (Peng-Robinson: LBM_EINVAL if its argument is negative).  0 = no wall
+     * (the default; rho_w then unused, default 1). */
+    int wall_rows;
+    double rho_w;
 } lbm_params;
 
 /* Observables of the current state (Sec. 3 measurements):
- * rho_l = rho at the centre node (nx/2, ny/2, nz/2); rho_g = rho at node 0;
+ * rho_l = rho at the centre node (nx/2, ny/2, nz/2); rho_g = rho at node 0
+ * (with a wall: rho_l at (nx/2, wall_rows), the first fluid node above the wall
+ * under the centre, rho_g at (0, ny - 1), the top fluid row; max_u, mean_u and
+ * mom then run over the fluid nodes, and mass over every node, which is what
+ * the scheme conserves);
  * dp = p(rho_l) - p(rho_g) with the bulk pressure p = c_s^2 rho + (G c_s'^2/2) psi^2
  * (= p_EOS for Peng-Robinson); max_u / mean_u = max and mean over cells of |u|,
  * u = (sum f c + F/2) / rho; mass = sum rho; mom = sum rho u; thickness =

@@ -387,6 +387,8 @@ int lbm_params_default(lbm_params* p)
     p->s_q = 1.9;
     p->precision = LBM_FP64;
     p->path = LBM_PATH_AUTO;
+    p->wall_rows = 0;
+    p->rho_w = 1.0;
     return LBM_OK;
 }
 
@@ -427,6 +429,14 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     }
     if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr))
         return fail(LBM_EINVAL, "dev_alloc and dev_free must be given together");
+    if (p->wall_rows != 0) {
+        if (li.D != 2) return fail(LBM_EUNSUPPORTED, "the wall is provided for the 2-D lattices");
+        if (p->path == LBM_PATH_ONE_PASS) return fail(LBM_EUNSUPPORTED, "the wall runs on the two-pass schedule");
+        const int need = li.reach > g ? li.reach : g;
+        if (p->wall_rows < need || p->wall_rows >= p->ny)
+            return fail(LBM_EINVAL, "wall_rows must lie in [%d, ny) (lattice reach and force radius)", need);
+        if (!(p->rho_w > 0.0) || !std::isfinite(p->rho_w)) return fail(LBM_EINVAL, "rho_w must be positive");
+    }
 
     KernelSet ks{};
     const int fp32 = p->precision == LBM_FP32_SHIFTED;
@@ -453,7 +463,7 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     c->N = (long long)p->nx * p->ny * nz;
     c->n_cand = 0;
     if (p->path != LBM_PATH_ONE_PASS) c->cand[c->n_cand++] = -1;
-    if (p->path != LBM_PATH_TWO_PASS)
+    if (p->path != LBM_PATH_TWO_PASS && p->wall_rows == 0)
         for (int v = 0; v < ks.n_onepass; ++v)
             if (p->nx % ks.onepass[v].nx_multiple == 0 &&
                 (ks.onepass[v].nx_exact == 0 || ks.onepass[v].nx_exact == p->nx))
@@ -531,6 +541,12 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     d.rate[2] = p->s_eps;
     d.rate[3] = p->s_q;
     d.err = c->err;
+    d.wall_rows = p->wall_rows;
+    if (p->wall_rows) {
+        d.psi_w = psi_host(c, p->rho_w);
+        if (!std::isfinite(d.psi_w))
+            return cleanup(fail(LBM_EINVAL, "psi of the wall density rho_w is not finite (Peng-Robinson argument below zero)"));
+    }
 
     // TMA descriptor of the ghosted psi buffer; the box is one fused-kernel
     // tile plus the halo (x: kGhostX each side, y/z: the stencil radius).
@@ -873,7 +889,7 @@ int lbm_observables(lbm_ctx* c, lbm_obs* out)
     o.mom[0] = r[kResMomX];
     o.mom[1] = r[kResMomY];
     o.mom[2] = r[kResMomZ];
-    o.mean_u = r[kResSumU] / (double)c->N;
+    o.mean_u = r[kResSumU] / (double)(c->N - (long long)c->prm.wall_rows * c->prm.nx * c->prm.nz);
     o.max_u = r[kResMaxU];
     o.rho_l = r[kResRhoCentre];
     o.rho_g = r[kResRhoOrigin];

@@ -932,8 +932,8 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
     for (int d = 0; d < n; ++d) {
         const lbm_params& p = ps[d];
         const int order = p.stencil == LBM_STENCIL_LATTICE ? 4 : p.stencil;
-        if (p.lattice != LBM_D2Q9 || p.psi != LBM_PSI_EXP || p.collision != LBM_BGK)
-            return set_last_error(LBM_EUNSUPPORTED, "lbm_batch_create: batches are D2Q9, exp psi, BGK");
+        if (p.lattice != LBM_D2Q9 || p.psi != LBM_PSI_EXP || p.collision != LBM_BGK || p.wall_rows != 0)
+            return set_last_error(LBM_EUNSUPPORTED, "lbm_batch_create: batches are D2Q9, exp psi, BGK, no wall");
         if ((p.precision == LBM_FP32_SHIFTED) != (fp32 != 0))
             return set_last_error(LBM_EINVAL, "lbm_batch_create: one precision per batch");
         if (p.nx < 8 || p.ny < 8 || p.nz != 1 || !(p.tau > 0.5) ||

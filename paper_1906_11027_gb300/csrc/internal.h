@@ -35,6 +35,8 @@ struct DevParams {
     double pr_alpha;     // alpha(T)
     double rate[4];      // MRT rates by class: 1/tau, s_e, s_eps, s_q
     unsigned* err;       // device error word
+    int wall_rows;       // rows y < wall_rows are solid (bounce-back); 0 = no wall
+    double psi_w;        // psi of the wall's virtual density
 };
 
 // Everything a launcher may need; unused fields are ignored.

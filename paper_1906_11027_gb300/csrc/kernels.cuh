@@ -377,9 +377,21 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
     }
 }
 
+// Index of the velocity opposite to c_b (c_opp = -c_b).
+template <int LAT>
+__host__ __device__ constexpr int opposite(int b)
+{
+    using L = Lattice<LAT>;
+    for (int k = 0; k < L::Q; ++k)
+        if (L::T.v[k][0] == -L::T.v[b][0] && L::T.v[k][1] == -L::T.v[b][1] && L::T.v[k][2] == -L::T.v[b][2])
+            return k;
+    return -1;
+}
+
 // ---- kernels -------------------------------------------------------------------------
 
-// rho and psi of every cell (pull gather), written with periodic ghosts.
+// rho and psi of every cell (pull gather), written with periodic ghosts.  A solid
+// node (y < wall_rows) carries the psi of the wall's virtual density.
 template <int LAT, class Real>
 __global__ void __launch_bounds__(256) k_psi(const Real* __restrict__ A, Real* __restrict__ psi, DevParams p)
 {
@@ -388,6 +400,10 @@ __global__ void __launch_bounds__(256) k_psi(const Real* __restrict__ A, Real* _
     const int y = blockIdx.y * 8 + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
+    if (y < p.wall_rows) {
+        store_psi<L::D>(psi, p, x, y, z, static_cast<Real>(p.psi_w));
+        return;
+    }
     Real f[L::Q];
     gather<LAT>(A, p, x, y, z, f);
     Real s = Real(0);
@@ -396,7 +412,9 @@ __global__ void __launch_bounds__(256) k_psi(const Real* __restrict__ A, Real* _
     store_psi<L::D>(psi, p, x, y, z, psi_of<LAT>(rho, p));
 }
 
-// Fused pull-stream / force / collide, psi tile staged by TMA.
+// Fused pull-stream / force / collide, psi tile staged by TMA.  A solid node
+// (y < wall_rows) takes no collision: it sends every population back the way
+// it came (standard bounce-back), f*_b = f_{-b}.
 template <int LAT, int ORD, int COLL, class Real, int TY, int TZ>
 __global__ void __launch_bounds__(32 * TY * TZ)
     k_fused(const __grid_constant__ CUtensorMap tmap, const Real* __restrict__ A, Real* __restrict__ B, DevParams p)
@@ -439,11 +457,20 @@ __global__ void __launch_bounds__(32 * TY * TZ)
         return;
     }
     if (!active) return;
+    const long long c = cell_of(p, x, y, z);
+    if (y < p.wall_rows) {
+        sfor<L::Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int ob = opposite<LAT>(b);
+            static_assert(ob >= 0, "velocity set without an opposite");
+            B[static_cast<long long>(b) * p.N + c] = f[ob];
+        });
+        return;
+    }
     const Real* tc = tile + ((tz + (D == 3 ? R : 0)) * SY + (ty + R)) * SX + (tx + kGhostX);
     Real F[3];
     force_from<LAT, ORD, Real, SX, SY>(tc, p.G, F);
     collide<LAT, COLL>(f, F, p);
-    const long long c = cell_of(p, x, y, z);
     sfor<L::Q>([&](auto bI) {
         constexpr int b = decltype(bI)::value;
         B[static_cast<long long>(b) * p.N + c] = f[b];
@@ -2029,6 +2056,11 @@ __global__ void __launch_bounds__(256)
         const int z = static_cast<int>(r / p.ny);
         double rho, mom[3];
         cell_macro<LAT, ORD>(A, psi, p, x, y, z, rho, mom);
+        if (y < p.wall_rows) {  // solid: its populations count in the mass only
+            if (!isfinite(rho)) bad = true;
+            v[0] += rho;
+            continue;
+        }
         const double ux = mom[0] / rho, uy = mom[1] / rho, uz = mom[2] / rho;
         const double um = sqrt(ux * ux + uy * uy + uz * uz);
         if (!isfinite(rho) || !isfinite(um)) bad = true;
@@ -2043,18 +2075,25 @@ __global__ void __launch_bounds__(256)
     block_reduce_obs(v, partials + static_cast<long long>(blockIdx.x) * kObsWidth);
 }
 
-// rho at the centre node, node 0 and along the x line through the centre.
+// rho along the x line through the centre (threads 0..nx-1), at the vapour
+// probe (thread nx) and at the liquid probe (thread nx+1).  Without a wall the
+// probes are node 0 and the centre node; with one they are (0, ny-1, 0), the
+// top fluid row, and (nx/2, wall_rows, nz/2), the first fluid node above the
+// wall under the centre.
 template <int LAT, class Real>
 __global__ void k_probe(const Real* __restrict__ A, DevParams p, double* __restrict__ res)
 {
     using L = Lattice<LAT>;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > p.nx) return;
+    if (i > p.nx + 1) return;
+    const int zc = (L::D == 3) ? p.nz / 2 : 0;
     int x, y, z, slot;
     if (i < p.nx) {
-        x = i; y = p.ny / 2; z = (L::D == 3) ? p.nz / 2 : 0; slot = kResLine + i;
+        x = i; y = p.ny / 2; z = zc; slot = kResLine + i;
+    } else if (i == p.nx) {
+        x = 0; y = p.wall_rows ? p.ny - 1 : 0; z = 0; slot = kResRhoOrigin;
     } else {
-        x = 0; y = 0; z = 0; slot = kResRhoOrigin;
+        x = p.nx / 2; y = p.wall_rows ? p.wall_rows : p.ny / 2; z = zc; slot = kResRhoCentre;
     }
     Real f[L::Q];
     gather<LAT>(A, p, x, y, z, f);
@@ -2062,7 +2101,6 @@ __global__ void k_probe(const Real* __restrict__ A, DevParams p, double* __restr
     sfor<L::Q>([&](auto bI) { s += static_cast<double>(f[decltype(bI)::value]); });
     const double rho = std::is_same<Real, float>::value ? p.rho_bar + s : s;
     res[slot] = rho;
-    if (i == p.nx / 2) res[kResRhoCentre] = rho;
 }
 
 template <int LAT, int ORD, class Real>
@@ -2077,9 +2115,10 @@ __global__ void __launch_bounds__(256) k_fields(const Real* __restrict__ A, cons
         const int z = static_cast<int>(r / p.ny);
         double rho, mom[3];
         cell_macro<LAT, ORD>(A, psi, p, x, y, z, rho, mom);
+        const bool solid = y < p.wall_rows;  // solid nodes report u = 0
         if (rho_out) rho_out[i] = rho;
         if (u_out)
-            for (int k = 0; k < 3; ++k) u_out[3 * i + k] = mom[k] / rho;
+            for (int k = 0; k < 3; ++k) u_out[3 * i + k] = solid ? 0.0 : mom[k] / rho;
     }
 }
 
@@ -2423,7 +2462,7 @@ cudaError_t launch_obs(const LaunchArgs& a, cudaStream_t s, int* nblocks)
 template <int LAT, class Real>
 cudaError_t launch_probe(const LaunchArgs& a, cudaStream_t s)
 {
-    const int n = a.p.nx + 1;
+    const int n = a.p.nx + 2;
     k_probe<LAT, Real><<<(n + 127) / 128, 128, 0, s>>>(static_cast<const Real*>(a.fin), a.p, a.res);
     return cudaGetLastError();
 }

@@ -15,7 +15,13 @@ interface thickness, i.e. the width of the region 1.05 rho_v <= rho <=
 0.95 rho_l with the run's own bulk densities: the node count per interface and
 the distance between the linearly interpolated crossings of the two levels.
 
-    python -m paper_1906_11027_gb300.experiments [--case flat] [--forcing edm] [--temps 0.7,0.8,0.9]
+--case wall (Fig. 6): a droplet on a flat wall at T/Tc = 0.9 (--temps), on a
+160 x 80 fluid region above a two-row solid band with standard bounce-back,
+for wall densities rho_w = 1.5 and 4.5 (--rho-w) and D2Q9 E4 / E8 and D2Q25;
+the line reports the contact angle of a circle fitted to the interface, the
+droplet's base and height, and the spurious currents.
+
+    python -m paper_1906_11027_gb300.experiments [--case flat|wall] [--forcing edm] [--temps 0.7,0.8,0.9]
 
 --forcing guo (the default) uses Guo's scheme with BGK; --forcing edm uses the
 exact-difference method the paper's own runs use.  The figures' data are not
@@ -106,6 +112,77 @@ def interface_thickness(line, rho_v, rho_l):
     return counts, float(np.mean(widths))
 
 
+def fit_contact_angle(rho, rows, level):
+    """Contact angle (degrees, through the liquid) of a sessile droplet: a
+    least-squares circle x^2 + y^2 + D x + E y + F = 0 through the interface
+    points (rho = level, linear interpolation along rows and columns, away
+    from the two rows next to the wall), measured against the wall surface
+    half-way between the last solid row and the first fluid row.  Returns
+    (angle, base width at the surface, height above it, radius)."""
+    ny, nx = rho.shape
+    pts = []
+    for y in range(rows + 2, ny):
+        line = rho[y]
+        if line.max() < level:
+            continue
+        i = int(np.argmax(line >= level))
+        if 0 < i:
+            pts.append((i - 1 + (level - line[i - 1]) / (line[i] - line[i - 1]), y))
+        j = nx - 1 - int(np.argmax(line[::-1] >= level))
+        if j < nx - 1:
+            pts.append((j + (line[j] - level) / (line[j] - line[j + 1]), y))
+    for x in range(nx):
+        col = rho[rows + 2:, x]
+        if col.max() < level:
+            continue
+        k = len(col) - 1 - int(np.argmax(col[::-1] >= level))
+        if k < len(col) - 1:
+            pts.append((x, rows + 2 + k + (col[k] - level) / (col[k] - col[k + 1])))
+    if len(pts) < 6:
+        raise ValueError(f"only {len(pts)} interface points at level {level:.4g}")
+    P = np.array(pts)
+    Am = np.column_stack([P[:, 0], P[:, 1], np.ones(len(P))])
+    D, E, F = np.linalg.lstsq(Am, -(P ** 2).sum(1), rcond=None)[0]
+    xc, yc = -D / 2.0, -E / 2.0
+    R = float(np.sqrt(xc * xc + yc * yc - F))
+    ys = rows - 0.5
+    h = yc - ys
+    cos_t = float(np.clip(-h / R, -1.0, 1.0))
+    base = 2.0 * float(np.sqrt(max(R * R - h * h, 0.0)))
+    return float(np.degrees(np.arccos(cos_t))), base, h + R, R
+
+
+def run_wall(a, T, Tc, rv, rl, name, lat, st, tau, coll, rho_w):
+    rows, nx, ny = 2, a.wall_nx, a.wall_ny + 2
+    dom = lbm.Domain(nx, ny, lattice=lat, stencil=st, psi=lbm.LBM_PSI_PENG_ROBINSON, T_over_Tc=T,
+                     G=-1.0, tau=tau, collision=coll, wall_rows=rows, rho_w=rho_w)
+    try:
+        x, y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+        r = np.hypot(x - nx // 2, y - rows)
+        rho0 = 0.5 * (rl + rv) - 0.5 * (rl - rv) * np.tanh(2.0 * (r - a.wall_r0) / 3.0)
+        rho0[:rows] = rho0[rows]
+        dom.init_from_rho(rho0)
+        steps, ok = dom.run_to_steady(1e-10, a.max_steps, 100)
+        u1 = dom.observables()["max_u"]
+        dom.step(a.extra)
+        o = dom.observables()
+        rho = dom.fields()["rho"][0]
+        r_l = float(rho[rows + 2:, nx // 2].max())
+        r_v = float(np.median(rho[rows + 2:, 0]))
+        row = dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), rho_w=rho_w, steps=steps,
+                   steady=ok, rho_l=r_l, rho_v=r_v, rho_min=float(rho[rows:].min()),
+                   rho_max=float(rho[rows:].max()), max_u=o["max_u"], mean_u=o["mean_u"], extra_steps=a.extra,
+                   max_u_drift=abs(o["max_u"] / u1 - 1.0))
+        try:
+            theta, base, height, R = fit_contact_angle(rho, rows, 0.5 * (r_l + r_v))
+            row.update(contact_angle_deg=theta, base=base, height=height, radius=R)
+        except ValueError as e:
+            row.update(fit_error=str(e))
+        return row
+    finally:
+        dom.close()
+
+
 def run_droplet(a, T, Tc, rv, rl, name, lat, st, tau, coll):
     dom = lbm.Domain(a.n, a.n, lattice=lat, stencil=st, psi=lbm.LBM_PSI_PENG_ROBINSON, T_over_Tc=T,
                      G=-1.0, tau=tau, collision=coll)
@@ -151,15 +228,20 @@ def main():
     ap.add_argument("--r0", type=float, default=15.0)
     ap.add_argument("--max-steps", type=int, default=200000)
     ap.add_argument("--forcing", choices=["guo", "edm"], default="guo")
-    ap.add_argument("--case", choices=["droplet", "flat"], default="droplet")
+    ap.add_argument("--case", choices=["droplet", "flat", "wall"], default="droplet")
+    ap.add_argument("--rho-w", default="1.5,4.5", help="wall densities of --case wall")
+    ap.add_argument("--wall-nx", type=int, default=160)
+    ap.add_argument("--wall-ny", type=int, default=80)
+    ap.add_argument("--wall-r0", type=float, default=25.0)
     ap.add_argument("--flat-nx", type=int, default=200)
     ap.add_argument("--extra", type=int, default=20000,
                     help="steps run after the steady test passes; the values reported are taken after them, "
                          "with their drift over those steps")
     ap.add_argument("--models", default="", help="comma-separated subset of: " + ", ".join(m[0] for m in MODELS))
     a = ap.parse_args()
-    models = [m for m in MODELS if not a.models or m[0] in a.models.split(",")]
-    run = run_flat if a.case == "flat" else run_droplet
+    wanted = a.models or ("D2Q9 E4,D2Q9 E8,D2Q25V" if a.case == "wall" else "")
+    models = [m for m in MODELS if not wanted or m[0] in wanted.split(",")]
+    run = {"flat": run_flat, "droplet": run_droplet}.get(a.case)
     coll = lbm.LBM_BGK_EDM if a.forcing == "edm" else lbm.LBM_BGK
     lbm.load()
     Tc = critical_T()
@@ -167,12 +249,17 @@ def main():
     for T in [float(t) for t in a.temps.split(",")]:
         rv, rl = maxwell(T, Tc)
         for name, lat, st, tau in models:
-            try:
-                row = run(a, T, Tc, rv, rl, name, lat, st, tau, coll)
-            except lbm.LbmError as e:
-                row = dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), case=a.case, error=str(e))
-            rows.append(row)
-            print(json.dumps(row), flush=True)
+            for rho_w in ([float(v) for v in a.rho_w.split(",")] if a.case == "wall" else [None]):
+                try:
+                    if a.case == "wall":
+                        row = run_wall(a, T, Tc, rv, rl, name, lat, st, tau, coll, rho_w)
+                    else:
+                        row = run(a, T, Tc, rv, rl, name, lat, st, tau, coll)
+                except lbm.LbmError as e:
+                    row = dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), case=a.case,
+                               rho_w=rho_w, error=str(e))
+                rows.append(row)
+                print(json.dumps(row), flush=True)
     return 0
 
 

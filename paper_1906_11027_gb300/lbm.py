@@ -39,6 +39,7 @@ class lbm_params(ctypes.Structure):
         ("precision", ctypes.c_int), ("path", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+        ("wall_rows", ctypes.c_int), ("rho_w", ctypes.c_double),
     ]
 
 
@@ -521,13 +522,14 @@ class Domain:
 
     def __init__(self, nx, ny, nz=1, lattice=LBM_D2Q9, stencil=LBM_STENCIL_LATTICE, psi=LBM_PSI_EXP,
                  T_over_Tc=0.0, G=-5.0, tau=1.0, collision=LBM_BGK, s_e=1.64, s_eps=1.54, s_q=1.9,
-                 precision=LBM_FP64, path=LBM_PATH_AUTO, stream=None, torch_alloc=False):
+                 precision=LBM_FP64, path=LBM_PATH_AUTO, stream=None, torch_alloc=False, wall_rows=0, rho_w=1.0):
         p = lbm_params_default()
         p.nx, p.ny, p.nz = nx, ny, nz
         p.lattice, p.stencil, p.psi = lattice, stencil, psi
         p.T_over_Tc, p.G, p.tau = T_over_Tc, G, tau
         p.collision, p.s_e, p.s_eps, p.s_q = collision, s_e, s_eps, s_q
         p.precision, p.path = precision, path
+        p.wall_rows, p.rho_w = wall_rows, rho_w
         self._alloc = None
         if stream is not None:
             p.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)

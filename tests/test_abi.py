@@ -67,6 +67,12 @@ def test_create_rejects_invalid_parameters(field, value, code):
      lbm.LBM_EUNSUPPORTED),
     (dict(psi=lbm.LBM_PSI_PENG_ROBINSON, T_over_Tc=0.8, G=1.0), lbm.LBM_EINVAL),
     (dict(collision=lbm.LBM_MRT, s_q=2.5), lbm.LBM_EINVAL),
+    (dict(lattice=lbm.LBM_D3Q19, nz=16, wall_rows=1), lbm.LBM_EUNSUPPORTED),
+    (dict(wall_rows=2, path=lbm.LBM_PATH_ONE_PASS), lbm.LBM_EUNSUPPORTED),
+    (dict(lattice=lbm.LBM_D2Q25, wall_rows=1), lbm.LBM_EINVAL),   # thinner than the reach of 2
+    (dict(stencil=lbm.LBM_ISO8, wall_rows=1), lbm.LBM_EINVAL),    # thinner than the force radius of 2
+    (dict(wall_rows=64), lbm.LBM_EINVAL),                          # no fluid left
+    (dict(wall_rows=2, rho_w=0.0), lbm.LBM_EINVAL),
 ])
 def test_create_rejects_unsupported_combinations(changes, code):
     p = lbm.lbm_params_default()
@@ -81,3 +87,20 @@ def test_null_arguments_rejected():
     assert lib.lbm_create(None, None) == lbm.LBM_EINVAL
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_destroy(None) == lbm.LBM_OK
+
+
+def test_params_layout_matches_the_header(tmp_path):
+    """The ctypes mirror of lbm_params has the C struct's size and field offsets."""
+    fields = [f[0] for f in lbm.lbm_params._fields_]
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "lbm.h"\nint main(void) {\n'
+                    '  printf("size %zu\\n", sizeof(lbm_params));\n'
+                    + "".join(f'  printf("{f} %zu\\n", offsetof(lbm_params, {f}));\n' for f in fields)
+                    + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(prog)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(lbm.lbm_params)
+    for f in fields:
+        assert int(out[f]) == getattr(lbm.lbm_params, f).offset, f

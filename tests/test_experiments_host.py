@@ -50,3 +50,21 @@ def test_maxwell_densities_match_the_independent_construction(t):
     rv2, rl2 = maxwell(t)
     assert rv == pytest.approx(rv2, rel=1e-6)
     assert rl == pytest.approx(rl2, rel=1e-6)
+
+
+@pytest.mark.parametrize("theta_deg", [50.0, 90.0, 130.0])
+def test_contact_angle_of_a_synthetic_cap(theta_deg):
+    """A circular cap of known contact angle, drawn as a smooth density field on
+    a grid above a two-row band (the wall surface half-way below the first fluid
+    row), is recovered by the circle fit to within 2 degrees."""
+    rows, nx, ny, R = 2, 160, 90, 30.0
+    ys = rows - 0.5
+    yc = ys - R * np.cos(np.radians(theta_deg))  # centre height for this angle
+    x, y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    d = np.hypot(x - 80.0, y - yc) - R
+    rho = 0.5 * (6.0 + 0.6) - 0.5 * (6.0 - 0.6) * np.tanh(2.0 * d / 4.0)
+    rho[y < ys] = 3.0
+    theta, base, height, radius = ex.fit_contact_angle(rho, rows, 3.3)
+    assert theta == pytest.approx(theta_deg, abs=2.0)
+    assert radius == pytest.approx(R, rel=0.02)
+    assert height == pytest.approx(R * (1.0 - np.cos(np.radians(theta_deg))), abs=1.0)
