@@ -2557,6 +2557,7 @@ KernelSet make_set()
                 add("onepass_row256x2_zauto_s2_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 0, 2, 2>, 1, 256);
                 add("onepass_rowp256x2_s2", &launch_onepass_rowp<LAT, ORD, COLL, Real, 256, 2, 2>, 1, 256);
                 add("onepass_rowp2_256x2_s2", &launch_onepass_rowp2<LAT, ORD, 256, 2, 2>, 1, 256);
+                add("onepass_rowp2_256x3_s2", &launch_onepass_rowp2<LAT, ORD, 256, 3, 2>, 1, 256);
                 add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 0>, 1, 128);
                 add("onepass_row128x4_z32_s3_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 1>, 1, 128);
                 add("onepass_row128x4_zauto_s3_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 0, 3, 2>, 1, 128);
