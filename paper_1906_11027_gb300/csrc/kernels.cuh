@@ -1615,9 +1615,12 @@ __device__ __forceinline__ void collide2_bgk(float2 (&f)[Lattice<LAT>::Q], const
 // with c_x = 0 come from shared memory as one 8-byte load per pair, the force and
 // collision run on float2 pairs with the packed FP32 instructions, and every
 // store is one 8-byte store.  Staging, item walk and producer are those of
-// k_onepass_rowp.
-template <int LAT, int ORD, int NX, int TY, int NSTG>
-__global__ void __launch_bounds__(NX / 2 * TY + 32, 1)
+// k_onepass_rowp.  PRODW = false drops the dedicated producer warp: the last
+// compute warp issues the stage copies right after each barrier and then
+// computes.  With 12 compute warps that keeps three warps per SM sub-partition
+// (a 13th warp would cap every thread at 128 registers).
+template <int LAT, int ORD, int NX, int TY, int NSTG, bool PRODW = true>
+__global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
     k_onepass_rowp2(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, int zc, int nitems)
 {
     using L = Lattice<LAT>;
@@ -1644,7 +1647,9 @@ __global__ void __launch_bounds__(NX / 2 * TY + 32, 1)
     const int tp = tid % (NX / 2), ty = tid / (NX / 2);  // pair index along x, row in the tile
     const int x0 = 2 * tp;                               // first cell of the pair
     const int lane = tid & 31;
-    const bool producer = tid >= NT;
+    const bool producer = PRODW && tid >= NT;
+    // the warp that issues the stage copies: the producer warp, else the last compute warp
+    const bool issuer = PRODW ? producer : (tid / 32 == NT / 32 - 1);
 
     if (tid == 0) {
         for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
@@ -1693,6 +1698,7 @@ __global__ void __launch_bounds__(NX / 2 * TY + 32, 1)
                 left -= n;
             }
         }
+        __syncwarp();
         ++issued;
         if (++p_next > p_last) {
             p_it += gridDim.x;
@@ -1756,7 +1762,7 @@ __global__ void __launch_bounds__(NX / 2 * TY + 32, 1)
         }
     };
 
-    if (producer) issue_upto(0);
+    if (issuer) issue_upto(0);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int y0 = (it % nty) * TY;
         const int m0 = (it / nty) * zc;
@@ -1767,14 +1773,14 @@ __global__ void __launch_bounds__(NX / 2 * TY + 32, 1)
 #pragma unroll
         for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
         __syncthreads();
-        if (producer) issue_upto(consumed);
+        if (issuer) issue_upto(consumed);
         const bool active = !producer && (y0 + ty) < p.ny;
         const int cell_xy = (y0 + ty) * NX + x0;
         for (int m = m0; m < m1; ++m) {
             if (!producer) psi_slab(m + R, consumed);
             ++consumed;
             __syncthreads();
-            if (producer) issue_upto(consumed);
+            if (issuer) issue_upto(consumed);
             if (active) {
                 // force (Eq. 1) of both cells from the psi ring, opposite vectors paired
                 const float* base[2 * R + 1];
@@ -2305,11 +2311,11 @@ inline int rowp_chunk(int nz, int nty, int nsm)
     return zc;
 }
 
-template <int LAT, int ORD, int NX, int TY, int NSTG>
+template <int LAT, int ORD, int NX, int TY, int NSTG, bool PRODW = true>
 cudaError_t launch_onepass_rowp2(const LaunchArgs& a, cudaStream_t s)
 {
     constexpr size_t dyn = sizeof(float) * NSTG * Lattice<LAT>::Q * (TY + 2) * NX;
-    auto kern = &k_onepass_rowp2<LAT, ORD, NX, TY, NSTG>;
+    auto kern = &k_onepass_rowp2<LAT, ORD, NX, TY, NSTG, PRODW>;
     if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     if (a.p.nx != NX) return cudaErrorInvalidValue;
     const int nty = (a.p.ny + TY - 1) / TY;
@@ -2320,7 +2326,7 @@ cudaError_t launch_onepass_rowp2(const LaunchArgs& a, cudaStream_t s)
     const int nitems = nty * ((a.p.nz + zc - 1) / zc);
     const int grid = nitems < nsm ? nitems : nsm;
     const auto P = make_pops<float, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
-    kern<<<grid, NX / 2 * TY + 32, dyn, s>>>(P, a.p, zc, nitems);
+    kern<<<grid, NX / 2 * TY + (PRODW ? 32 : 0), dyn, s>>>(P, a.p, zc, nitems);
     return cudaGetLastError();
 }
 
@@ -2558,6 +2564,7 @@ KernelSet make_set()
                 add("onepass_rowp256x2_s2", &launch_onepass_rowp<LAT, ORD, COLL, Real, 256, 2, 2>, 1, 256);
                 add("onepass_rowp2_256x2_s2", &launch_onepass_rowp2<LAT, ORD, 256, 2, 2>, 1, 256);
                 add("onepass_rowp2_256x3_s2", &launch_onepass_rowp2<LAT, ORD, 256, 3, 2>, 1, 256);
+                add("onepass_rowp2_256x3_s2_np", &launch_onepass_rowp2<LAT, ORD, 256, 3, 2, false>, 1, 256);
                 add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 0>, 1, 128);
                 add("onepass_row128x4_z32_s3_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 1>, 1, 128);
                 add("onepass_row128x4_zauto_s3_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 0, 3, 2>, 1, 128);
