@@ -697,7 +697,8 @@ int occupancy_seg(int)
 {
     auto kern = &k_batch_step_seg<TX, ZC, NSTG>;
     constexpr size_t dyn = seg_dyn_bytes<TX, ZC, NSTG>();
-    if (dyn > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+    // the 48 KB default covers static plus dynamic shared memory: set the limit for any request
+    if (dyn > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX + 32, dyn);
     return occ;

@@ -29,13 +29,15 @@ namespace lbm {
 constexpr double kPrA = 2.0 / 49.0;  // Peng-Robinson a, b (R = 1), Sec. 3
 constexpr double kPrB = 2.0 / 21.0;
 
-// Raises a kernel's dynamic shared-memory limit where it exceeds the 48 KB
-// default, once per (kernel, device): the attribute belongs to the device, and a
-// process may drive several.
+// Sets a kernel's dynamic shared-memory limit to its request, once per (kernel,
+// device): the attribute belongs to the device, and a process may drive several.
 template <class K>
 cudaError_t ensure_dyn_smem(K kern, size_t dyn)
 {
-    if (dyn <= 48 * 1024) return cudaSuccess;
+    // The default limit (48 KB) covers static plus dynamic shared memory, so a
+    // kernel whose dynamic part fits under 48 KB can still need the attribute
+    // once its static arrays are added: set it for every dynamic request.
+    if (dyn == 0) return cudaSuccess;
     static std::mutex mu;
     static std::set<std::pair<const void*, int>> done;
     int dev = 0;
@@ -412,9 +414,8 @@ __global__ void __launch_bounds__(256) k_psi(const Real* __restrict__ A, Real* _
     store_psi<L::D>(psi, p, x, y, z, psi_of<LAT>(rho, p));
 }
 
-// Fused pull-stream / force / collide, psi tile staged by TMA.  A solid node
-// (y < wall_rows) takes no collision: it sends every population back the way
-// it came (standard bounce-back), f*_b = f_{-b}.
+// Fused pull-stream / force / collide, psi tile staged by TMA.  (With a wall,
+// k_bounce then rewrites the rows of the solid band.)
 template <int LAT, int ORD, int COLL, class Real, int TY, int TZ>
 __global__ void __launch_bounds__(32 * TY * TZ)
     k_fused(const __grid_constant__ CUtensorMap tmap, const Real* __restrict__ A, Real* __restrict__ B, DevParams p)
@@ -457,24 +458,39 @@ __global__ void __launch_bounds__(32 * TY * TZ)
         return;
     }
     if (!active) return;
+    const Real* tc = tile + ((tz + (D == 3 ? R : 0)) * SY + (ty + R)) * SX + (tx + kGhostX);
+    Real F[3];
+    force_from<LAT, ORD, Real, SX, SY>(tc, p.G, F);
+    collide<LAT, COLL>(f, F, p);
     const long long c = cell_of(p, x, y, z);
-    if (y < p.wall_rows) {
+    sfor<L::Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        B[static_cast<long long>(b) * p.N + c] = f[b];
+    });
+}
+
+// Standard bounce-back on the solid band y < wall_rows (2-D): a solid node takes
+// no collision and sends every population back the way it came, f*_b = f_{-b}.
+// Runs after k_fused on the same stream and overwrites what that kernel wrote
+// for the band, so the fluid kernels carry no wall test.
+template <int LAT, class Real>
+__global__ void __launch_bounds__(256) k_bounce(const Real* __restrict__ A, Real* __restrict__ B, DevParams p)
+{
+    using L = Lattice<LAT>;
+    const long long n = static_cast<long long>(p.nx) * p.wall_rows;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % p.nx), y = static_cast<int>(i / p.nx);
+        Real f[L::Q];
+        gather<LAT>(A, p, x, y, 0, f);
+        const long long c = cell_of(p, x, y, 0);
         sfor<L::Q>([&](auto bI) {
             constexpr int b = decltype(bI)::value;
             constexpr int ob = opposite<LAT>(b);
             static_assert(ob >= 0, "velocity set without an opposite");
             B[static_cast<long long>(b) * p.N + c] = f[ob];
         });
-        return;
     }
-    const Real* tc = tile + ((tz + (D == 3 ? R : 0)) * SY + (ty + R)) * SX + (tx + kGhostX);
-    Real F[3];
-    force_from<LAT, ORD, Real, SX, SY>(tc, p.G, F);
-    collide<LAT, COLL>(f, F, p);
-    sfor<L::Q>([&](auto bI) {
-        constexpr int b = decltype(bI)::value;
-        B[static_cast<long long>(b) * p.N + c] = f[b];
-    });
 }
 
 // ---- one-pass schedule ------------------------------------------------------------
@@ -1577,8 +1593,10 @@ __device__ __forceinline__ void collide2_bgk(float2 (&f)[Lattice<LAT>::Q], const
     const float2 uy = mul2(fma2(p2(0.5f), F[1], jy), inv_rho);
     const float2 uz = mul2(fma2(p2(0.5f), F[2], jz), inv_rho);
     constexpr double cs2 = L::cs2;
-    const float2 usq = mul2(fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))), p2(float(0.5 / cs2)));
-    const float2 uF = fma2(ux, F[0], fma2(uy, F[1], mul2(uz, F[2])));
+    constexpr bool k3 = L::D == 3;  // 2-D: no z terms (u_z = F_z = 0)
+    const float2 usq = k3 ? mul2(fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))), p2(float(0.5 / cs2)))
+                          : mul2(fma2(ux, ux, mul2(uy, uy)), p2(float(0.5 / cs2)));
+    const float2 uF = k3 ? fma2(ux, F[0], fma2(uy, F[1], mul2(uz, F[2]))) : fma2(ux, F[0], mul2(uy, F[1]));
     const float2 omega = p2(float(p.omega));
     const float2 pref = p2(float(p.pref));
     const float2 orho = mul2(omega, rho);
@@ -1811,6 +1829,183 @@ __global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
             for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
         }
         __syncthreads();
+    }
+    if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
+}
+
+// Packed-pair form of the segment schedule k_onepass_seg (FP32 BGK, 2-D reach-1
+// lattices): a compute thread owns the x-adjacent cells (2t, 2t + 1) of the
+// tile, so the directions with c_x = 0 come from the staged segment as one
+// 8-byte load per pair, psi, the force and the collision run on float2 pairs
+// with the packed FP32 instructions, and every store is one 8-byte store.
+// Staging, stage reuse and the producer warp are those of k_onepass_seg.
+template <int LAT, int ORD, int TX, int ZC, int NSTG>
+__global__ void __launch_bounds__(TX / 2 + 32, 1)
+    k_onepass_seg2(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, int ntx)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<2, ORD>;
+    constexpr int R = S::radius;
+    constexpr int Q = L::Q;
+    static_assert(L::D == 2 && L::reach == 1, "segment staging is written for 2-D reach-1 lattices");
+    constexpr int NT = TX / 2;       // compute threads
+    constexpr int XP = 4;            // 16 bytes of floats on each side of the tile
+    static_assert(XP >= R + 1 && TX % XP == 0 && NT % 32 == 0, "x pad / tile");
+    constexpr int W = TX + 2 * XP;   // staged segment length (even: the pairs stay 8-byte aligned)
+    constexpr int EX = TX + 2 * R;   // psi ring row
+    constexpr int NS = 2 * R + 2;
+    constexpr int STG = Q * W;
+    static_assert(NSTG >= R + 2 && NSTG >= 2 * R, "one row in flight; the 2R warm-up rows staged at once");
+    __shared__ float ring[NS * EX];
+    __shared__ alignas(8) unsigned long long bars[NSTG];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    float* stage = reinterpret_cast<float*>(dyn_smem);  // [NSTG][Q][W]
+
+    const int tile = blockIdx.x % ntx;
+    const int chunk = blockIdx.x / ntx;
+    const int x0 = tile * TX;
+    const int nm = p.ny;
+    const int m0 = chunk * ZC;
+    const int m1 = (m0 + ZC < nm) ? m0 + ZC : nm;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const bool producer = tid >= NT;
+    const int cx0 = 2 * tid;  // tile offset of the pair's first cell
+
+    if (tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    int cby = 0;
+    const float* src_b = nullptr;
+    sfor<Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int vy = L::T.v[b][1];
+        if (lane == b) {
+            cby = vy;
+            src_b = P.in[b];
+        }
+    });
+    const int base = m0 - R;
+    auto issue = [&](int s) {
+        const int slot = (s - base) % NSTG;
+        const uint32_t bar = smem_u32(&bars[slot]);
+        if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(STG * sizeof(float)));
+        __syncwarp();
+        if (lane < Q) {
+            fence_proxy_async_smem();
+            const float* row = src_b + static_cast<long long>(wrap_any(s - cby, nm)) * p.nx;
+            uint32_t dst = smem_u32(stage + slot * STG + lane * W);
+            int xs = x0 - XP, left = W;
+            while (left > 0) {
+                const int x = wrap_any(xs, p.nx);
+                const int n = (p.nx - x < left) ? p.nx - x : left;
+                bulk_g2s(dst, row + x, static_cast<uint32_t>(n * sizeof(float)), bar);
+                dst += static_cast<uint32_t>(n * sizeof(float));
+                xs += n;
+                left -= n;
+            }
+        }
+    };
+    uint32_t phase = 0;
+    bool ok = true;
+    auto stage_of = [&](int s) { return stage + ((s - base) % NSTG) * STG; };
+    auto wait_stage = [&](int s) {
+        const int slot = (s - base) % NSTG;
+        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        phase ^= 1u << slot;
+    };
+    // f of the cell at tile offset cx (-R .. TX + R - 1) from stage st (pull)
+    auto load_cell = [&](const float* st, int cx, float (&f)[Q]) {
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int vx = L::T.v[b][0];
+            f[b] = st[b * W + cx + XP - vx];
+        });
+    };
+    // f of the pair (cx0, cx0 + 1): c_x = 0 as one 8-byte load, shifted directions as two words
+    auto load_pair = [&](const float* st, float2 (&f)[Q]) {
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int vx = L::T.v[b][0];
+            const float* rb = st + b * W + XP + cx0;
+            if (vx == 0)
+                f[b] = *reinterpret_cast<const float2*>(rb);
+            else
+                f[b] = make_float2(rb[-vx], rb[1 - vx]);
+        });
+    };
+    auto rho_psi = [&](const float (&f)[Q]) {
+        float sum = 0.f;
+        sfor<Q>([&](auto bI) { sum += f[decltype(bI)::value]; });
+        return psi_of<LAT>(static_cast<float>(p.rho_bar) + sum, p);
+    };
+    auto psi_slab = [&](int s) {
+        wait_stage(s);
+        const float* st = stage_of(s);
+        float* dst = ring + ring_slot(s, NS) * EX;
+        float2 f[Q];
+        load_pair(st, f);
+        float2 sum = p2(0.f);
+        sfor<Q>([&](auto bI) { sum = add2(sum, f[decltype(bI)::value]); });
+        const float rb = static_cast<float>(p.rho_bar);
+        dst[cx0 + R] = psi_of<LAT>(rb + sum.x, p);
+        dst[cx0 + 1 + R] = psi_of<LAT>(rb + sum.y, p);
+        if (tid < 2 * R) {
+            const int cx = (tid < R) ? tid - R : TX + tid - R;
+            float fs[Q];
+            load_cell(st, cx, fs);
+            dst[cx + R] = rho_psi(fs);
+        }
+    };
+
+    int next = base;
+    const int last = m1 - 1 + R;
+    if (producer)
+        for (; next <= last && next < base + NSTG; ++next) issue(next);
+    if (!producer)
+        for (int s = m0 - R; s < m0 + R; ++s) psi_slab(s);
+    __syncthreads();
+    // slabs below m0 are consumed (psi only): slab k may refill slab k - NSTG's stage
+    if (producer)
+        for (; next <= last && next < m0 + NSTG; ++next) issue(next);
+
+    const bool active = !producer && (x0 + cx0) < p.nx;  // nx even: the pair's second cell is inside too
+    for (int m = m0; m < m1; ++m) {
+        if (!producer) psi_slab(m + R);
+        __syncthreads();
+        // every thread is past the collision of row m - 1
+        if (producer)
+            for (; next <= last && next <= m - 1 + NSTG; ++next) issue(next);
+        if (active) {
+            float2 f[Q];
+            load_pair(stage_of(m), f);
+            // force (Eq. 1) of both cells from the psi ring, opposite vectors paired
+            const float* rowp[2 * R + 1];
+#pragma unroll
+            for (int k = 0; k < 2 * R + 1; ++k) rowp[k] = ring + ring_slot(m - R + k, NS) * EX + cx0 + R;
+            float2 ax = p2(0.f), ay = p2(0.f);
+            sfor<S::n / 2>([&](auto kI) {
+                constexpr int a = 2 * decltype(kI)::value;
+                constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1];
+                constexpr double wt = S::T.w[a] * L::cs2;
+                const float* pp = rowp[ey + R] + ex;
+                const float* pm = rowp[R - ey] - ex;
+                const float2 d = sub2(make_float2(pp[0], pp[1]), make_float2(pm[0], pm[1]));
+                if (ex != 0) ax = fma2(p2(float(wt * ex)), d, ax);
+                if (ey != 0) ay = fma2(p2(float(wt * ey)), d, ay);
+            });
+            const float2 gp = mul2(p2(float(-p.G)), make_float2(rowp[R][0], rowp[R][1]));
+            const float2 F[3] = {mul2(gp, ax), mul2(gp, ay), p2(0.f)};
+            collide2_bgk<LAT>(f, F, p);
+            const int c = m * p.nx + x0 + cx0;
+            sfor<Q>([&](auto bI) {
+                constexpr int b = decltype(bI)::value;
+                __stcs(reinterpret_cast<float2*>(P.out[b] + c), f[b]);
+            });
+        }
     }
     if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
 }
@@ -2271,6 +2466,11 @@ cudaError_t launch_fused(const LaunchArgs& a, cudaStream_t s)
     const dim3 grd((a.p.nx + 31) / 32, (a.p.ny + TY - 1) / TY, Lattice<LAT>::D == 3 ? (a.p.nz + TZ - 1) / TZ : 1);
     k_fused<LAT, ORD, COLL, Real, TY, TZ><<<grd, blk, 0, s>>>(*a.tmap, static_cast<const Real*>(a.fin),
                                                              static_cast<Real*>(a.fout), a.p);
+    if (Lattice<LAT>::D == 2 && a.p.wall_rows > 0) {
+        const long long n = static_cast<long long>(a.p.nx) * a.p.wall_rows;
+        k_bounce<LAT, Real><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+            static_cast<const Real*>(a.fin), static_cast<Real*>(a.fout), a.p);
+    }
     return cudaGetLastError();
 }
 
@@ -2394,6 +2594,20 @@ cudaError_t launch_onepass_seg(const LaunchArgs& a, cudaStream_t s)
     const long long nblocks = static_cast<long long>(ntx) * ((a.p.ny + ZC - 1) / ZC);
     const auto P = make_pops<Real, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
     kern<<<static_cast<unsigned>(nblocks), TX + 32, dyn, s>>>(P, a.p, ntx);
+    return cudaGetLastError();
+}
+
+template <int LAT, int ORD, int TX, int ZC, int NSTG>
+cudaError_t launch_onepass_seg2(const LaunchArgs& a, cudaStream_t s)
+{
+    constexpr size_t dyn = sizeof(float) * NSTG * Lattice<LAT>::Q * (TX + 8);
+    auto kern = &k_onepass_seg2<LAT, ORD, TX, ZC, NSTG>;
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
+    if (a.p.nx % 4 != 0) return cudaErrorInvalidValue;
+    const int ntx = (a.p.nx + TX - 1) / TX;
+    const long long nblocks = static_cast<long long>(ntx) * ((a.p.ny + ZC - 1) / ZC);
+    const auto P = make_pops<float, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
+    kern<<<static_cast<unsigned>(nblocks), TX / 2 + 32, dyn, s>>>(P, a.p, ntx);
     return cudaGetLastError();
 }
 
@@ -2595,6 +2809,10 @@ KernelSet make_set()
                 add("onepass_seg256_z64_s6", &launch_onepass_seg<LAT, ORD, COLL, Real, 256, 64, 6>, 4);
                 add("onepass_seg128_z64_s8", &launch_onepass_seg<LAT, ORD, COLL, Real, 128, 64, 8>, 4);
                 add("onepass_seg512_z64_s6", &launch_onepass_seg<LAT, ORD, COLL, Real, 512, 64, 6>, 4);
+                add("onepass_seg2_256_z64_s6", &launch_onepass_seg2<LAT, ORD, 256, 64, 6>, 4);
+                add("onepass_seg2_512_z64_s6", &launch_onepass_seg2<LAT, ORD, 512, 64, 6>, 4);
+                if constexpr (Stencil<2, ORD>::radius <= 2)
+                    add("onepass_seg2_512_z64_s4", &launch_onepass_seg2<LAT, ORD, 512, 64, 4>, 4);
             }
         }
     }

@@ -330,6 +330,8 @@ def test_one_pass_ragged_3d_against_oracle(lbm):
     (1, (21, 19, 37), 6, 1),
     (1, (20, 16, 33), 4, 0),
     (0, (1, 45, 300), 4, 1),
+    (0, (1, 70, 520), 8, 1),    # radius-2 stencil: every segment variant, ragged tiles and chunks
+    (0, (1, 37, 260), 10, 1),   # radius 3, the widest halo the segment staging takes
     (0, (1, 33, 70), 10, 0),
     (3, (1, 37, 150), 0, 1),
 ])
