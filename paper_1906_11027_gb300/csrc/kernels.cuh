@@ -2210,25 +2210,68 @@ __device__ __forceinline__ double psi_at(const Real* __restrict__ psi, const Dev
     return static_cast<double>(psi[(static_cast<long long>(z + gz) * p.psy + (y + p.g)) * p.psx + (x + kGhostX)]);
 }
 
+// Density and momentum sums of one cell in FP64 (exact for FP32-stored values,
+// so small currents keep their resolution); zero velocity components add nothing.
+template <int LAT, class Real>
+__device__ __forceinline__ void cell_sums(const Real* __restrict__ A, const DevParams& p, int x, int y, int z,
+                                          double& rho, double (&j)[3])
+{
+    using L = Lattice<LAT>;
+    Real f[L::Q];
+    gather<LAT>(A, p, x, y, z, f);
+    double s = 0.0;
+    j[0] = j[1] = j[2] = 0.0;
+    sfor<L::Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        const double fb = static_cast<double>(f[b]);
+        s += fb;
+        sfor<3>([&](auto iI) {
+            constexpr int i = decltype(iI)::value;
+            constexpr int c = L::T.v[b][i];
+            if constexpr (c == 1) j[i] += fb;
+            else if constexpr (c == -1) j[i] -= fb;
+            else if constexpr (c != 0) j[i] += fb * c;
+        });
+    });
+    rho = std::is_same<Real, float>::value ? p.rho_bar + s : s;
+}
+
+// Eq. 1 force of one cell in FP32 from an FP32 psi buffer (observables of FP32
+// storage: relative error ~1e-7, off the slow FP64 pipe).
+template <int LAT, int ORD>
+__device__ __forceinline__ void cell_force_f32(const float* __restrict__ psi, const DevParams& p, int x, int y,
+                                               int z, float (&F)[3])
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<L::D, ORD>;
+    const int gz = (L::D == 3) ? p.g : 0;
+    const float* c0 = psi + (static_cast<long long>(z + gz) * p.psy + (y + p.g)) * p.psx + (x + kGhostX);
+    const long long sy = p.psx, sz = static_cast<long long>(p.psx) * p.psy;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    sfor<S::n / 2>([&](auto kI) {
+        constexpr int a = 2 * decltype(kI)::value;
+        constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1], ez = S::T.v[a][2];
+        constexpr float wt = static_cast<float>(S::T.w[a] * L::cs2);
+        const long long o = ez * sz + ey * sy + ex;
+        const float d = c0[o] - c0[-o];
+        if (ex != 0) ax = fmaf(wt * ex, d, ax);
+        if (ey != 0) ay = fmaf(wt * ey, d, ay);
+        if (ez != 0) az = fmaf(wt * ez, d, az);
+    });
+    const float gp = -static_cast<float>(p.G) * c0[0];
+    F[0] = gp * ax;
+    F[1] = gp * ay;
+    F[2] = gp * az;
+}
+
 template <int LAT, int ORD, class Real>
 __device__ __forceinline__ void cell_macro(const Real* __restrict__ A, const Real* __restrict__ psi,
                                            const DevParams& p, int x, int y, int z, double& rho, double (&mom)[3])
 {
     using L = Lattice<LAT>;
     using S = Stencil<L::D, ORD>;
-    Real f[L::Q];
-    gather<LAT>(A, p, x, y, z, f);
-    double s = 0.0, j[3] = {0.0, 0.0, 0.0};
-    sfor<L::Q>([&](auto bI) {
-        constexpr int b = decltype(bI)::value;
-        constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
-        const double fb = static_cast<double>(f[b]);
-        s += fb;
-        j[0] += fb * cx;
-        j[1] += fb * cy;
-        j[2] += fb * cz;
-    });
-    rho = std::is_same<Real, float>::value ? p.rho_bar + s : s;
+    double j[3];
+    cell_sums<LAT>(A, p, x, y, z, rho, j);
     double acc[3] = {0.0, 0.0, 0.0};
     sfor<S::n>([&](auto aI) {
         constexpr int a = decltype(aI)::value;
@@ -2255,15 +2298,28 @@ __global__ void __launch_bounds__(256)
         const long long r = i / p.nx;
         const int y = static_cast<int>(r % p.ny);
         const int z = static_cast<int>(r / p.ny);
-        double rho, mom[3];
-        cell_macro<LAT, ORD>(A, psi, p, x, y, z, rho, mom);
+        double rho, mom[3], um;
+        if constexpr (std::is_same<Real, float>::value) {
+            // FP32 storage: FP64 sums, FP32 force, 1/rho and |u|
+            double j[3];
+            cell_sums<LAT>(A, p, x, y, z, rho, j);
+            float F[3];
+            cell_force_f32<LAT, ORD>(psi, p, x, y, z, F);
+            for (int k = 0; k < 3; ++k) mom[k] = j[k] + 0.5 * static_cast<double>(F[k]);
+            const float inv = 1.0f / static_cast<float>(rho);
+            const float ux = static_cast<float>(mom[0]) * inv, uy = static_cast<float>(mom[1]) * inv,
+                        uz = static_cast<float>(mom[2]) * inv;
+            um = static_cast<double>(sqrtf(ux * ux + uy * uy + uz * uz));
+        } else {
+            cell_macro<LAT, ORD>(A, psi, p, x, y, z, rho, mom);
+            const double ux = mom[0] / rho, uy = mom[1] / rho, uz = mom[2] / rho;
+            um = sqrt(ux * ux + uy * uy + uz * uz);
+        }
         if (y < p.wall_rows) {  // solid: its populations count in the mass only
             if (!isfinite(rho)) bad = true;
             v[0] += rho;
             continue;
         }
-        const double ux = mom[0] / rho, uy = mom[1] / rho, uz = mom[2] / rho;
-        const double um = sqrt(ux * ux + uy * uy + uz * uz);
         if (!isfinite(rho) || !isfinite(um)) bad = true;
         v[0] += rho;
         v[1] += mom[0];

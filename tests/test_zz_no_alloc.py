@@ -5,9 +5,12 @@ device memory is reserved up front by another framework's pool, or cudaMalloc is
 off limits on their latency-critical path).  This entry point takes the
 population buffer and a host array and keeps its block partials in a static
 device array.  The test calls it twice in a row through the C ABI and compares
-both results with lbm_observables (which uses the context's allocated scratch)
-at the FP64 parity tolerance of the other tests, 1e-12 relative.  The file is
-named so that pytest collects it last.
+both results with lbm_observables (which uses the context's allocated scratch):
+the mass at the FP64 parity tolerance of the other tests, 1e-12 relative, and
+the momentum at 1e-12 in FP64 storage.  With FP32 storage the observables take
+each cell's force in FP32, so the half-force sum they add, zero in exact
+arithmetic, is zero only up to that round-off, bounded from the cells' own
+forces.  The file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -48,7 +51,15 @@ def test_noalloc_matches_observables_twice(lbm, precision):
     # the observables' momentum adds sum_x F / 2, which is zero up to round-off
     scale = np.abs(ref[1:3]).max()
     assert scale > 1.0
-    assert np.abs(first[1:] - ref[1:]).max() <= 1e-12 * scale
+    bound = 1e-12 * scale
+    if precision == 1:
+        # FP32 storage: each cell's force is taken in FP32 (a few operations,
+        # well inside 2^-21 of |F|); F = 2 (rho u - j) from the FP64 fields
+        fld, f = dom.fields(), dom.get_f()[:, 0]
+        j = np.einsum("bi,byx->iyx", C9, f)
+        F = 2.0 * (fld["rho"][0][None] * np.moveaxis(fld["u"][0][..., :2], -1, 0) - j)
+        bound += 0.5 * 2.0 ** -21 * np.abs(F).sum()
+    assert np.abs(first[1:] - ref[1:]).max() <= bound
 
 
 def test_noalloc_rejects_oversized_domain(lbm):
