@@ -241,24 +241,21 @@ def main():
     a = ap.parse_args()
     wanted = a.models or ("D2Q9 E4,D2Q9 E8,D2Q25V" if a.case == "wall" else "")
     models = [m for m in MODELS if not wanted or m[0] in wanted.split(",")]
-    run = {"flat": run_flat, "droplet": run_droplet}.get(a.case)
+    run = {"droplet": run_droplet, "flat": run_flat, "wall": run_wall}[a.case]
+    wall_densities = [float(v) for v in a.rho_w.split(",")] if a.case == "wall" else [None]
     coll = lbm.LBM_BGK_EDM if a.forcing == "edm" else lbm.LBM_BGK
     lbm.load()
     Tc = critical_T()
-    rows = []
     for T in [float(t) for t in a.temps.split(",")]:
         rv, rl = maxwell(T, Tc)
         for name, lat, st, tau in models:
-            for rho_w in ([float(v) for v in a.rho_w.split(",")] if a.case == "wall" else [None]):
+            for rho_w in wall_densities:
+                extra = (rho_w,) if a.case == "wall" else ()
                 try:
-                    if a.case == "wall":
-                        row = run_wall(a, T, Tc, rv, rl, name, lat, st, tau, coll, rho_w)
-                    else:
-                        row = run(a, T, Tc, rv, rl, name, lat, st, tau, coll)
+                    row = run(a, T, Tc, rv, rl, name, lat, st, tau, coll, *extra)
                 except lbm.LbmError as e:
                     row = dict(T_over_Tc=T, model=name, forcing=a.forcing, tau=round(tau, 4), case=a.case,
                                rho_w=rho_w, error=str(e))
-                rows.append(row)
                 print(json.dumps(row), flush=True)
     return 0
 
