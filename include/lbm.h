@@ -77,7 +77,9 @@ typedef enum { LBM_BGK = 0, LBM_MRT = 1, LBM_BGK_EDM = 2 } lbm_collision;
  * reductions stay in double. */
 typedef enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 } lbm_precision;
 
-/* Kernel schedule of one time step; every schedule gives bit-identical results.
+/* Kernel schedule of one time step.  Every schedule computes the same step:
+ * bit-identical in FP64 and among the one-cell-per-thread FP32 schedules, within
+ * FP32 round-off for the packed-pair FP32 ones (see lbm_schedule_report).
  * LBM_PATH_TWO_PASS: a psi kernel writes psi (with periodic ghosts) to its own
  * buffer, then the fused stream-collide-force kernel stages psi tiles plus the
  * stencil halo into shared memory by TMA.  LBM_PATH_ONE_PASS: one kernel
