@@ -37,6 +37,12 @@ WORKLOADS = {
     "d3q19_256_fp32_iso6": dict(lattice=1, shape=(256, 256, 256), precision=1, stencil=6, R=40.0,
                                 desc="D3Q19 BGK FP32-shifted 256^3 periodic, psi=1-exp(-rho), G=-5, "
                                      "6th-order 3-D force stencil, centred droplet R=40"),
+    "d3q19_256_fp32_mrt": dict(lattice=1, shape=(256, 256, 256), precision=1, stencil=4, R=40.0, collision=1,
+                               desc="D3Q19 MRT (rates 1/tau, s_e=1.64, s_eps=1.54, s_q=1.9) FP32-shifted 256^3 "
+                                    "periodic, psi=1-exp(-rho), G=-5, 4th-order 3-D force stencil, centred droplet R=40"),
+    "d2q9_8192_fp32_mrt": dict(lattice=0, shape=(1, 8192, 8192), precision=1, stencil=4, R=2048.0, collision=1,
+                               desc="D2Q9 MRT (rates 1/tau, s_e=1.64, s_eps=1.54, s_q=1.9) FP32-shifted 8192^2 "
+                                    "periodic, psi=1-exp(-rho), G=-5, 4th-order stencil, centred droplet R=2048"),
     "d2q9_8192_fp32": dict(lattice=0, shape=(1, 8192, 8192), precision=1, stencil=4, R=2048.0,
                            desc="D2Q9 BGK FP32-shifted 8192^2 periodic, psi=1-exp(-rho), G=-5, 4th-order stencil, "
                                 "centred droplet R=2048"),
@@ -212,7 +218,8 @@ def oracle_sample_run(wl, budget_s, steps, fill_budget=False):
     dim = 3 if nz > 1 else 2
     lat = {0: oracle.D2Q9, 1: oracle.D3Q19}[wl["lattice"]]
     side = 48 if dim == 3 else 64
-    probe = oracle.Sim(lat, side, side, side if dim == 3 else 1, stencil=wl["stencil"], G=G, tau=TAU)
+    coll = {0: oracle.BGK, 1: oracle.MRT}[wl.get("collision", 0)]
+    probe = oracle.Sim(lat, side, side, side if dim == 3 else 1, stencil=wl["stencil"], G=G, tau=TAU, coll=coll)
     probe.init_droplet(RHO_L, RHO_G, wl["R"] * side / nx, WIDTH)
     t0 = time.perf_counter()
     probe.step(2)
@@ -222,7 +229,7 @@ def oracle_sample_run(wl, budget_s, steps, fill_budget=False):
     L = max(16, min(nx, (L // 8) * 8))
     if fill_budget:
         steps = max(steps, int(budget_s * rate / L ** dim))
-    sim = oracle.Sim(lat, L, L, L if dim == 3 else 1, stencil=wl["stencil"], G=G, tau=TAU)
+    sim = oracle.Sim(lat, L, L, L if dim == 3 else 1, stencil=wl["stencil"], G=G, tau=TAU, coll=coll)
     sim.init_droplet(RHO_L, RHO_G, wl["R"] * L / nx, WIDTH)
     t0 = time.perf_counter()
     sim.step(steps)
@@ -280,6 +287,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream()
     path = {"auto": lbm.LBM_PATH_AUTO, "two": lbm.LBM_PATH_TWO_PASS, "one": lbm.LBM_PATH_ONE_PASS}[args.path]
     dom = lbm.Domain(nx, ny, nz, lattice=wl["lattice"], stencil=wl["stencil"], G=G, tau=TAU,
+                     collision=wl.get("collision", lbm.LBM_BGK),
                      precision=wl["precision"], stream=stream, torch_alloc=True, path=path)
     if args.schedule:  # pin a schedule (profiling runs), else the autotuner picks
         dom.set_schedule(args.schedule)

@@ -43,6 +43,30 @@ MUTATIONS = [
     ("wall one row too thick", "static int is_solid(const or_sim* s, int y) { return y < s->wall_rows; }",
      "static int is_solid(const or_sim* s, int y) { return y <= s->wall_rows; }",
      "tests/test_oracle_wall.py::test_wall_force_is_one_sided"),
+    ("init width W in place of W/2", "0.5 * (rho_l + rho_g) - 0.5 * (rho_l - rho_g) * tanh(2.0 * (r - R) / W);",
+     "0.5 * (rho_l + rho_g) - 0.5 * (rho_l - rho_g) * tanh((r - R) / W);",
+     "tests/test_oracle_init.py::test_droplet_initial_state_is_the_tanh_profile"),
+    ("init centre at (n - 1)/2", "double d = (double)i - (double)(n / 2);",
+     "double d = (double)i - 0.5 * (double)(n - 1);",
+     "tests/test_oracle_init.py::test_droplet_initial_state_is_the_tanh_profile"),
+    ("flat slab width W in place of W/2", "tanh(2.0 * (r - 0.25 * L) / W);", "tanh((r - 0.25 * L) / W);",
+     "tests/test_oracle_init.py::test_flat_initial_state_is_the_tanh_slab"),
+    ("MRT s_e and s_eps swapped", "double r[9] = { st, s_e, s_eps, st, s_q, st, s_q, st, st };",
+     "double r[9] = { st, s_eps, s_e, st, s_q, st, s_q, st, st };",
+     "tests/test_oracle_mrt.py::test_each_moment_relaxes_at_its_own_rate"),
+    ("MRT s_q missing from the D3Q19 m moments", "st, s_eps, st, s_eps, st, st, st, s_q, s_q, s_q };",
+     "st, s_eps, st, s_eps, st, st, st, s_eps, s_eps, s_eps };",
+     "tests/test_oracle_mrt.py::test_each_moment_relaxes_at_its_own_rate"),
+    ("MRT D3Q19 m_x polynomial sign", "case 16: return (y * y - z * z) * x;", "case 16: return (y * y + z * z) * x;",
+     "tests/test_oracle_mrt.py::test_each_moment_relaxes_at_its_own_rate"),
+    ("thickness band edge", "if (r >= 1.05 * rg && r <= 0.95 * rl) thick += 1.0;",
+     "if (r >= 1.05 * rg && r <= 0.9 * rl) thick += 1.0;",
+     "tests/test_oracle_init.py::test_thickness_counts_band_nodes_of_a_flat_slab"),
+    ("thickness counted from one", "double thick = 0.0;", "double thick = 1.0;",
+     "tests/test_oracle_init.py::test_thickness_counts_band_nodes_of_a_flat_slab"),
+    ("thickness along the wrong axis", "double r = s->rho[cell_index(s, x, s->ny / 2, s->nz / 2)];",
+     "double r = s->rho[cell_index(s, s->nx / 2, x % s->ny, s->nz / 2)];",
+     "tests/test_oracle_init.py::test_thickness_counts_band_nodes_of_a_flat_slab"),
 ]
 
 

@@ -8,8 +8,10 @@ theory independent of the code.
   equal-area rule over 0.6 <= T/Tc <= 0.95 spans a density ratio "4 to 800".
 - Flat interface with psi = 1 - exp(-rho), 4th-order stencil and Guo forcing:
   the coexistence densities satisfy the mechanical-stability condition
-  int (p0 - p) psi'/psi^(1+eps) drho = 0 with eps = 0, the value the discrete
-  pressure tensor of the nearest-neighbour force gives.
+  int (p0 - p) psi'/psi^(1+eps) drho = 0 with eps = 0, the published value for
+  this force and forcing scheme (Shan, Phys. Rev. E 77, 066702, 2008, for the
+  pressure tensor; Li, Luo & Li, Phys. Rev. E 86, 016709, 2012, for eps under
+  Guo's forcing); the eps = 1 densities lie outside the tolerances.
 - A static droplet obeys Laplace's law dp = sigma / R (linear in 1/R, intercept
   near zero).
 """
@@ -138,6 +140,10 @@ def test_flat_interface_coexistence(G, tol_g):
     assert o["rho_g"] == pytest.approx(rg_th, rel=tol_g)
     assert abs(o["dp"]) < 1e-6  # flat: the bulk pressures are equal
     assert o["max_u"] < 1e-6
+    # the eps = 1 form of the condition is excluded by a wide margin
+    rg_1, rl_1 = mechanical_stability(G, eps=1.0)
+    assert abs(o["rho_g"] / rg_1 - 1) > 10 * tol_g
+    assert abs(o["rho_l"] / rl_1 - 1) > 10 * 5e-4
 
 
 @pytest.mark.slow

@@ -3,8 +3,11 @@
 mechanical_stability: coexistence densities (rho_g, rho_l) of a flat interface
 for psi = 1 - exp(-rho) and p = c_s^2 rho + (G c_s^2 / 2) psi^2, from equal
 bulk pressures and  int_{rho_g}^{rho_l} (p0 - p) psi' / psi^(1 + eps) drho = 0;
-eps = 0 is the value the discrete pressure tensor of the nearest-neighbour
-force gives with Guo forcing.
+eps = 0 is the published value for the nearest-neighbour force with Guo
+forcing: Shan, Phys. Rev. E 77, 066702 (2008) derives the force's pressure
+tensor, whose gradient part has no (grad psi)^2 term, and Li, Luo & Li,
+Phys. Rev. E 86, 016709 (2012) give eps = -2 alpha / beta for Guo's scheme,
+alpha and beta the coefficients of (grad psi)^2 and psi lap(psi) in it.
 """
 import numpy as np
 from scipy.integrate import quad
