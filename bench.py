@@ -40,6 +40,9 @@ WORKLOADS = {
     "d3q19_256_fp32_mrt": dict(lattice=1, shape=(256, 256, 256), precision=1, stencil=4, R=40.0, collision=1,
                                desc="D3Q19 MRT (rates 1/tau, s_e=1.64, s_eps=1.54, s_q=1.9) FP32-shifted 256^3 "
                                     "periodic, psi=1-exp(-rho), G=-5, 4th-order 3-D force stencil, centred droplet R=40"),
+    "d3q19_200_fp32": dict(lattice=1, shape=(200, 200, 200), precision=1, stencil=4, R=31.25,
+                           desc="D3Q19 BGK FP32-shifted 200^3 periodic (a row length that is not a power of two), "
+                                "psi=1-exp(-rho), G=-5, 4th-order 3-D force stencil, centred droplet R=31.25"),
     "d2q9_8192_fp32_mrt": dict(lattice=0, shape=(1, 8192, 8192), precision=1, stencil=4, R=2048.0, collision=1,
                                desc="D2Q9 MRT (rates 1/tau, s_e=1.64, s_eps=1.54, s_q=1.9) FP32-shifted 8192^2 "
                                     "periodic, psi=1-exp(-rho), G=-5, 4th-order stencil, centred droplet R=2048"),
@@ -386,22 +389,25 @@ def run_ours(args, world, rank, local):
         line["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                                 "sample": sample,
                                 "single_thread": oracle_single_thread(args.workload, args.cpu_budget / 2)}
+    if rank == 0 and world == 1 and not args.no_sweep:
+        line["sweep"] = sweep_summary(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
 
 
-def run_sweep(args):
+def sweep_compare(args, n_domains, with_warm, train_domains, epochs, details):
     """Batched FP32 sweep (one persistent-kernel CUDA graph for all domains) against
     plain FP64 one-domain-per-launch runs of the same domains, both to steady state.
-    With --sweep-warm the batched arm starts every domain from the learned warm
-    start, the network trained beforehand on the steady states of a separate draw
-    of domains (another seed), so the timed domains are unseen."""
+    With with_warm the batched sweep also runs from the learned warm start, the
+    network trained beforehand on the steady states of a separate draw of
+    domains (another seed), so the timed domains are unseen.  Returns the
+    result line (a dict)."""
     import torch
     from paper_1906_11027_gb300 import inputs, lbm, warmstart
 
     lbm.load()
-    doms = inputs.sweep_domains(args.sweep_domains)
+    doms = inputs.sweep_domains(n_domains)
     cells = sum(d["nx"] * d["ny"] for d in doms)
     torch.cuda.synchronize()
     # warm the kernels (module load) outside the timed regions
@@ -410,16 +416,16 @@ def run_sweep(args):
     w.close()
     K = 100
     net, train_info = None, None
-    if args.sweep_warm:
+    if with_warm:
         t0 = time.perf_counter()
-        tdoms = inputs.sweep_domains(args.ws_train_domains, seed=inputs.SWEEP_SEED + 1)
+        tdoms = inputs.sweep_domains(train_domains, seed=inputs.SWEEP_SEED + 1)
         tb = lbm.Batch(tdoms, precision=lbm.LBM_FP32_SHIFTED)
         _, tobs, _ = tb.run_to_steady(1e-10, args.sweep_max_steps, K)
         Xt, yt, Xv, yv, _ = warmstart.dataset_from_batch(tb, tdoms, tobs)
         tb.close()
         t_gen = time.perf_counter() - t0
         t0 = time.perf_counter()
-        net, loss = warmstart.train(Xt, yt, epochs=args.ws_epochs)
+        net, loss = warmstart.train(Xt, yt, epochs=epochs)
         torch.cuda.synchronize()
         train_info = {"train_domains": len(tdoms), "train_seed": inputs.SWEEP_SEED + 1,
                       "train_samples": int(len(yt)), "profile_sweep_s": round(t_gen, 2),
@@ -454,7 +460,7 @@ def run_sweep(args):
                     fallbacks=fallbacks, schedule=sched)
 
     plain = batched_arm(False)
-    warm = batched_arm(True) if args.sweep_warm else None
+    warm = batched_arm(True) if with_warm else None
     main_arm = warm if warm else plain
     t_batch, steps32, obs32, ok32 = main_arm["t"], main_arm["steps"], main_arm["obs"], main_arm["ok"]
     tiny = [None] * main_arm["tiny"]
@@ -516,7 +522,7 @@ def run_sweep(args):
         "per_domain": [[d["nx"], round(d["G"], 3), d["tau"], d["stencil"], round(d["R"], 1), int(steps32[i]),
                         int(steps64[i]), float("%.4g" % obs32[i]["max_u"]), float("%.4g" % obs64[i]["max_u"]),
                         int(plain["steps"][i]), float("%.4g" % plain["obs"][i]["max_u"])]
-                       for i, d in enumerate(doms)] if args.sweep_details else None,
+                       for i, d in enumerate(doms)] if details else None,
         "max_u_rel_diff": {"max": round(max(ratio), 4), "median": round(float(np.median(ratio)), 4),
                            "within_5pct": sum(1 for r in ratio if r <= 0.05), "compared": len(finite),
                            "both_below_fp64_threshold": len(small),
@@ -530,8 +536,40 @@ def run_sweep(args):
         "arms": arms,
         "warm_start_training": train_info,
     }
+    return line
+
+
+def run_sweep(args):
+    line = sweep_compare(args, args.sweep_domains, args.sweep_warm, args.ws_train_domains, args.ws_epochs,
+                         args.sweep_details)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def sweep_summary(args):
+    """The sweep half of the metric, bounded for the default line: a
+    --sweep-sub-domains draw of the parameter sweep (seed 11027), batched FP32
+    from the tanh and from the learned start (network trained first on an
+    equal draw of seed 11028) against plain FP64 one domain per launch, all to
+    steady state, with the per-domain max|u| agreement classified."""
+    t0 = time.perf_counter()
+    ln = sweep_compare(args, args.sweep_sub_domains, True, args.sweep_sub_domains, args.sweep_sub_epochs, False)
+    a = ln["arms"]
+    return {
+        "metric": "sweep_time_to_steady_s", "unit": "s", "domains": ln["config"]["domains"],
+        "cells": ln["config"]["cells"], "seed": ln["config"]["seed"],
+        "batched_fp32_tanh_s": a["batched_fp32_tanh_s"], "batched_fp32_warm_s": a["batched_fp32_warm_s"],
+        "warm_init_s": a["warm_init_s"], "fp64_one_domain_per_launch_s": ln["baseline_fp64_one_domain_per_launch_s"],
+        "speedup_tanh": round(ln["baseline_fp64_one_domain_per_launch_s"] / a["batched_fp32_tanh_s"], 2),
+        "speedup_warm": ln["speedup"],
+        "steps_total": {"tanh_fp32": a["steps_total_tanh"], "warm_fp32": a["steps_total_warm"],
+                        "fp64": ln["steps"]["fp64_total"]},
+        "max_u_within_5pct_warm_vs_fp64": ln["max_u_rel_diff"],
+        "max_u_within_5pct_tanh_vs_fp64": ln["max_u_rel_diff_tanh_fp32_vs_fp64"],
+        "warm_start_training": ln["warm_start_training"],
+        "rule": ln["config"]["rule"],
+        "wall_s": round(time.perf_counter() - t0, 1),
+    }
 
 
 def run_warmstart(args):
@@ -622,6 +660,11 @@ def main():
     ap.add_argument("--schedule", default=None, help="pin the step schedule by name instead of autotuning")
     ap.add_argument("--sweep", action="store_true", help="time the batched sweep instead of the step")
     ap.add_argument("--sweep-domains", type=int, default=64)
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="leave the bounded sweep comparison out of the step benchmark's line")
+    ap.add_argument("--sweep-sub-domains", type=int, default=64,
+                    help="domains of the sweep comparison carried by the step benchmark's line")
+    ap.add_argument("--sweep-sub-epochs", type=int, default=40)
     ap.add_argument("--sweep-max-steps", type=int, default=200000)
     ap.add_argument("--sweep-details", action="store_true")
     ap.add_argument("--sweep-warm", action="store_true",

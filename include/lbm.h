@@ -334,11 +334,15 @@ int lbm_init_droplet_learned(lbm_ctx* ctx, lbm_mlp* net, double R, double rho_l,
  *             post-collision buffer that lbm_device_state returns; double for
  *             LBM_FP64, float deviations from w_b rho_bar for LBM_FP32_SHIFTED
  *   lattice, precision, nx, ny, nz, rho_bar   describe that buffer (rho_bar is
- *             ignored for LBM_FP64)
+ *             ignored for LBM_FP64; for a context's buffer it is the value
+ *             lbm_reference_density returns)
  *   stream    cudaStream_t the kernels run on (NULL: the legacy default stream);
  *             the call synchronises it
- *   out_host  4 doubles: sum over cells of rho, then of sum_b f_b c_b (x, y, z),
- *             the momentum before the half-force term
+ *   out_host  4 doubles: sum over every cell of rho, then of sum_b f_b c_b
+ *             (x, y, z), the momentum before the half-force term.  With a wall
+ *             the sums include the solid band (lbm_observables takes its
+ *             momentum over the fluid nodes only; its mass also covers every
+ *             cell)
  * The block partials live in one static device array of about 512 KiB that
  * every GPU loading the library keeps until exit, so at most 16,777,216 cells
  * are accepted (LBM_EINVAL beyond, with a message in lbm_last_error()).  The
@@ -347,6 +351,23 @@ int lbm_init_droplet_learned(lbm_ctx* ctx, lbm_mlp* net, double R, double rho_l,
  * on the GPU race and must be serialised by the caller. */
 int lbm_moments_noalloc(const void* f_dev, int lattice, int precision, int nx, int ny, int nz,
                         double rho_bar, void* stream, double* out_host);
+
+/* The reference density rho_bar of a context's FP32 deviation storage
+ * (populations kept as f_b - w_b rho_bar): the mean density of the state the
+ * context was last initialised or loaded from.  0 for LBM_FP64 contexts.  This
+ * is the value to pass to lbm_moments_noalloc with lbm_device_state's buffer. */
+int lbm_reference_density(lbm_ctx* ctx, double* rho_bar);
+
+/* Failure-detection check (the paper has no counterpart).  Launches one block
+ * whose thread waits, through the same time-bounded mbarrier wait that the
+ * staged step kernels use, on a shared-memory barrier that nothing completes
+ * and against which no copy is issued.  The wait gives up after about 2 s; the
+ * kernel records the timeout in the context's device error word and returns
+ * with nothing in flight, and the call reports the word exactly as a step's
+ * readback would: LBM_ETIMEOUT is the expected result (any other code means
+ * the wait or the reporting is broken).  The context stays usable afterwards.
+ * Synchronises the context's stream. */
+int lbm_diag_wait_timeout(lbm_ctx* ctx);
 
 const char* lbm_strerror(int code);
 const char* lbm_last_error(void);

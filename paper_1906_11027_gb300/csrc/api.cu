@@ -171,6 +171,7 @@ struct lbm_ctx {
     {
         LaunchArgs a{};
         a.p = dp;
+        finish_params(a.p);
         a.fin = buf[cur];
         a.fout = buf[cur ^ 1];
         a.psi = psi;
@@ -466,7 +467,8 @@ int lbm_create(const lbm_params* p, lbm_ctx** out)
     if (p->path != LBM_PATH_TWO_PASS && p->wall_rows == 0)
         for (int v = 0; v < ks.n_onepass; ++v)
             if (p->nx % ks.onepass[v].nx_multiple == 0 &&
-                (ks.onepass[v].nx_exact == 0 || ks.onepass[v].nx_exact == p->nx))
+                (ks.onepass[v].nx_exact == 0 || ks.onepass[v].nx_exact == p->nx) &&
+                (ks.onepass[v].nx_max == 0 || p->nx <= ks.onepass[v].nx_max))
                 c->cand[c->n_cand++] = v;
     if (c->n_cand == 0) {
         delete c;
@@ -904,6 +906,24 @@ int lbm_observables(lbm_ctx* c, lbm_obs* out)
     if (!std::isfinite(o.mass) || !std::isfinite(o.max_u)) return fail(LBM_ENONFINITE, "non-finite observables");
     *out = o;
     return LBM_OK;
+}
+
+int lbm_reference_density(lbm_ctx* c, double* rho_bar)
+{
+    if (!c || !rho_bar) return fail(LBM_EINVAL, "NULL argument");
+    *rho_bar = c->dp.rho_bar;
+    return LBM_OK;
+}
+
+int lbm_diag_wait_timeout(lbm_ctx* c)
+{
+    if (!c) return fail(LBM_EINVAL, "NULL argument");
+    if (int rc = set_device(c)) return rc;
+    LBM_CK(launch_wait_probe(c->err, c->stream));
+    unsigned w = 0;
+    if (int rc = check_err_word(c, &w)) return rc;
+    if (int rc = err_code_of(w)) return rc;
+    return fail(LBM_ECUDA, "the probe's wait on a barrier that nothing completes did not give up");
 }
 
 int lbm_run_to_steady(lbm_ctx* c, double tol, int64_t max_steps, int64_t check_every, int64_t* steps_out)

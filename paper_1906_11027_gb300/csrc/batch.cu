@@ -38,6 +38,7 @@ struct BatchDom {
     long long off;   // element offset of the domain in each population pool
     long long poff;  // element offset of the domain in the psi scratch field (two-pass shape)
     double G, omega, pref, rho_bar;
+    float G_f, omega_f, pref_f, rho_bar_f;  // FP32 copies (set with the doubles on the host)
 };
 
 __device__ __forceinline__ DevParams dom_params(const BatchDom& d)
@@ -51,6 +52,10 @@ __device__ __forceinline__ DevParams dom_params(const BatchDom& d)
     p.omega = d.omega;
     p.pref = d.pref;
     p.rho_bar = d.rho_bar;
+    p.G_f = d.G_f;
+    p.omega_f = d.omega_f;
+    p.pref_f = d.pref_f;
+    p.rho_bar_f = d.rho_bar_f;
     p.psi_kind = 0;
     return p;
 }
@@ -123,7 +128,7 @@ __device__ void batch_item(const Real* __restrict__ A, Real* __restrict__ Bo, co
                 f[b] = st[b * TX];
             });
             Real F[3];
-            force_ring<kLatD2Q9, ORD, Real, EX, E, NS>(ring, m, tid + R, 0, p.G, F);
+            force_ring<kLatD2Q9, ORD, Real, EX, E, NS>(ring, m, tid + R, 0, par<Real>(p.G, p.G_f), F);
             collide<kLatD2Q9, 0>(f, F, p);
             const int c = m * p.nx + ix;
             sfor<Q>([&](auto bI) {
@@ -217,7 +222,7 @@ __device__ __forceinline__ void batch_item_seg(const float* __restrict__ A, floa
     auto stage_of = [&](int s) { return stage + ((s - base) % NSTG) * STG; };
     auto wait_stage = [&](int s) {
         const int slot = (s - base) % NSTG;
-        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        if (ok && !mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;  // after a timeout, stop waiting
         phase ^= 1u << slot;
     };
     auto load_cell = [&](const float* st, int cx, float (&f)[Q]) {
@@ -264,7 +269,7 @@ __device__ __forceinline__ void batch_item_seg(const float* __restrict__ A, floa
             float f[Q];
             load_cell(stage_of(m), tid, f);
             float F[3];
-            force_ring<kLatD2Q9, ORD, float, EX, EX, NS>(ring, m, tid + R, 0, p.G, F);
+            force_ring<kLatD2Q9, ORD, float, EX, EX, NS>(ring, m, tid + R, 0, p.G_f, F);
             collide<kLatD2Q9, 0>(f, F, p);
             const long long c = static_cast<long long>(m) * p.nx + x0 + tid;
             sfor<Q>([&](auto bI) {
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(TX + 32) k_batch_step_seg(const BatchDom* __re
 // results are bitwise the same) and collides.  Work item = 256 consecutive cells
 // of one domain.
 template <int ORD, class Real>
-__device__ __forceinline__ void force_global(const Real* __restrict__ psi, int nx, int ny, int x, int y, double G,
+__device__ __forceinline__ void force_global(const Real* __restrict__ psi, int nx, int ny, int x, int y, Real G,
                                              Real (&F)[3])
 {
     using L = Lattice<kLatD2Q9>;
@@ -336,7 +341,7 @@ __device__ __forceinline__ void force_global(const Real* __restrict__ psi, int n
         if (ex != 0) ax += Real(wt * ex) * d;
         if (ey != 0) ay += Real(wt * ey) * d;
     });
-    const Real gp = -Real(G) * psi[y * nx + x];
+    const Real gp = -G * psi[y * nx + x];
     F[0] = gp * ax;
     F[1] = gp * ay;
     F[2] = gp * az;
@@ -371,7 +376,7 @@ __device__ __forceinline__ void fused2_cell(const Real* __restrict__ A, const Re
     Real f[kQ9];
     gather<kLatD2Q9>(A, p, x, y, 0, f);
     Real F[3];
-    force_global<ORD, Real>(psi, p.nx, p.ny, x, y, p.G, F);
+    force_global<ORD, Real>(psi, p.nx, p.ny, x, y, par<Real>(p.G, p.G_f), F);
     collide<kLatD2Q9, 0>(f, F, p);
     sfor<kQ9>([&](auto bI) {
         constexpr int b = decltype(bI)::value;
@@ -992,6 +997,10 @@ int lbm_batch_create(const lbm_params* ps, const double* init, int n, lbm_batch*
                 }
             m.rho_bar = sum / ((double)p.nx * p.ny);
         }
+        m.G_f = static_cast<float>(m.G);
+        m.omega_f = static_cast<float>(m.omega);
+        m.pref_f = static_cast<float>(m.pref);
+        m.rho_bar_f = static_cast<float>(m.rho_bar);
         off += (long long)kQ9 * p.nx * p.ny;
         off = (off + 63) / 64 * 64;  // 256-byte aligned domains
         m.poff = poff;

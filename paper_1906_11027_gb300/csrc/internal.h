@@ -37,7 +37,29 @@ struct DevParams {
     unsigned* err;       // device error word
     int wall_rows;       // rows y < wall_rows are solid (bounce-back); 0 = no wall
     double psi_w;        // psi of the wall's virtual density
+    // Derived by finish_params(): the MRT correction factors omega - s per rate
+    // class (class 0 relaxes at omega, so its factor is 0), and FP32 copies of
+    // the scalars the FP32 kernels use, so they convert nothing per cell.
+    double dmrt[4];
+    float omega_f, pref_f, rho_bar_f, G_f;
+    float om1_f;  // 1 - omega, rounded once from double
+    float dmrt_f[4];
 };
+
+// Fills the derived fields of p from the others; call after any change to
+// omega, pref, rho_bar, G or rate.
+__host__ __device__ inline void finish_params(DevParams& p)
+{
+    for (int c = 0; c < 4; ++c) {
+        p.dmrt[c] = (c == 0) ? 0.0 : p.omega - p.rate[c];
+        p.dmrt_f[c] = static_cast<float>(p.dmrt[c]);
+    }
+    p.omega_f = static_cast<float>(p.omega);
+    p.pref_f = static_cast<float>(p.pref);
+    p.rho_bar_f = static_cast<float>(p.rho_bar);
+    p.G_f = static_cast<float>(p.G);
+    p.om1_f = static_cast<float>(1.0 - p.omega);
+}
 
 // Everything a launcher may need; unused fields are ignored.
 struct LaunchArgs {
@@ -63,8 +85,9 @@ struct StepVariant {
     cudaError_t (*fn)(const LaunchArgs&, cudaStream_t);
     int nx_multiple;     // nx must be a multiple of this (two cells per thread, 16-byte rows)
     int nx_exact;        // nonzero: the variant is compiled for this nx only (whole rows in shared memory)
+    int nx_max;          // nonzero: the variant takes rows of at most this many cells (shared-memory size)
 };
-constexpr int kMaxVariants = 32;
+constexpr int kMaxVariants = 40;
 
 // One set of launchers per (lattice, stencil order, collision, precision).
 struct KernelSet {
@@ -91,6 +114,10 @@ cudaError_t launch_sum_partials(const double* partials, int nblocks, int width, 
                                 cudaStream_t s);
 cudaError_t launch_mean(const double* x, long long n, double* partials, int nblocks_max,
                         double* res, cudaStream_t s);
+
+// Failure-detection check (diag.cu): one block waits on an mbarrier that nothing
+// completes, through the step kernels' bounded wait, and sets kErrTimeout in *err.
+cudaError_t launch_wait_probe(unsigned* err, cudaStream_t s);
 
 // Warm-start network (mlp.cu): evaluates the network's density at T signed
 // distances evenly spaced over [-dmax, dmax] for (G, tau, order, R) into table_dev.

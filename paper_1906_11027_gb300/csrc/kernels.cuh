@@ -79,13 +79,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait: every try_wait suspends for a hardware-chosen interval, so the
-// bound is a few seconds at most.  Returns false if it ran out.
+// Bounded wait.  try_wait suspends for an interval the hardware chooses, so
+// the bound is kept in time rather than in tries: the wait gives up once the
+// global nanosecond timer has advanced kWaitLimitNs past its first failed try
+// (no staged copy legitimately takes that long).  Returns false if it ran out.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
-    for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar)
 {
@@ -211,7 +223,7 @@ __device__ __forceinline__ void store_psi(Real* __restrict__ psi, const DevParam
 
 // ---- force (Eq. 1) from a psi view with compile-time strides -------------------
 template <int LAT, int ORD, class Real, int SX, int SY>
-__device__ __forceinline__ void force_from(const Real* tc, double G, Real (&F)[3])
+__device__ __forceinline__ void force_from(const Real* tc, Real G, Real (&F)[3])
 {
     using L = Lattice<LAT>;
     using S = Stencil<L::D, ORD>;
@@ -227,10 +239,156 @@ __device__ __forceinline__ void force_from(const Real* tc, double G, Real (&F)[3
         if (ey != 0) ay += Real(wt * ey) * d;
         if (ez != 0) az += Real(wt * ez) * d;
     });
-    const Real gp = -Real(G) * tc[0];
+    const Real gp = -G * tc[0];
     F[0] = gp * ax;
     F[1] = gp * ay;
     F[2] = gp * az;
+}
+
+// ---- value helpers shared by the scalar and the packed-pair collision --------
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ double vmul(double a, double b) { return a * b; }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <class V> __device__ __forceinline__ V vsplat(double x);
+template <> __device__ __forceinline__ double vsplat<double>(double x) { return x; }
+template <> __device__ __forceinline__ float vsplat<float>(double x) { return static_cast<float>(x); }
+template <> __device__ __forceinline__ float2 vsplat<float2>(double x)
+{
+    return make_float2(static_cast<float>(x), static_cast<float>(x));
+}
+// acc + C x for a compile-time integer C (no operation for C = 0)
+template <int C, class V>
+__device__ __forceinline__ V macc(V acc, V x)
+{
+    if constexpr (C == 0) return acc;
+    else if constexpr (C == 1) return vadd(acc, x);
+    else if constexpr (C == -1) return vsub(acc, x);
+    else return vfma(vsplat<V>(double(C)), x, acc);
+}
+// A scalar parameter in the kernel's precision (FP32 kernels read the FP32 copy).
+template <class Real>
+__device__ __forceinline__ Real par(double d, float f)
+{
+    if constexpr (std::is_same<Real, float>::value) return f; else return d;
+}
+
+// ---- MRT as a correction of the BGK update -------------------------------------
+// With m_eq := M feq and Guo's source in moment space, the MRT update is
+//   m* = m - S (m - m_eq) + (I - S/2) m_src,
+// and the BGK update is the same with S = omega I.  Their difference is
+// (omega I - S)(m - m_eq + m_src/2), so
+//   f*_b = f_BGK,b + sum_k M_kb t_k,  t_k = (omega - s_k)/|M_k|^2 m_k(g),  g = f - feq + src/2,
+// where only the moments whose rate differs from omega contribute (the
+// conserved ones have m_k(g) = 0: sum g = 0 and sum g c = j - rho u + F/2 = 0).
+// m_k(f) comes from the pair sums P = f_b + f_b+1 (even rows) or differences
+// D = f_b - f_b+1 (odd rows), b = 2p + 1; the equilibrium and source moments
+// are closed forms in the compile-time tensors A, B, C of Mrt<LAT>::T:
+//   even rows: m_k(g) = m_k(f) - A_k (rho' - u.v/(2 cs2)) - u.C_k.v/(2 cs4)
+//   odd rows:  m_k(g) = m_k(f) - B_k.j/cs2
+// with v = j - F/2 (= rho u - F) and rho' = rho, or rho - rho_bar for FP32
+// deviations (whose m_k(f) lacks the rho_bar A_k of the stored offset).
+template <int LAT, class V>
+__device__ __forceinline__ void mrt_moments_g(V f0, const V (&P)[(Lattice<LAT>::Q - 1) / 2],
+                                              const V (&D)[(Lattice<LAT>::Q - 1) / 2], V r0, const V (&j)[3],
+                                              const V (&u)[3], const V (&v)[3], const V (&dm)[4],
+                                              V (&t)[Lattice<LAT>::Q])
+{
+    using L = Lattice<LAT>;
+    using MB = Mrt<LAT>;
+    constexpr int Q = L::Q;
+    constexpr int NP = (Q - 1) / 2;
+    constexpr int DIM = L::D;
+    constexpr double cs2 = L::cs2;
+    V uv = vmul(u[0], v[0]);
+    uv = vfma(u[1], v[1], uv);
+    if constexpr (DIM == 3) uv = vfma(u[2], v[2], uv);
+    const V e0 = vfma(uv, vsplat<V>(-0.5 / cs2), r0);
+    sfor<Q>([&](auto kI) {
+        constexpr int k = decltype(kI)::value;
+        constexpr int rc = MB::B.rate_class[k];
+        if constexpr (rc != 0) {
+            constexpr int par_k = MB::T.parity[k];
+            static_assert(par_k != 0, "every non-conserved MRT row is even or odd under c -> -c");
+            V m = vsplat<V>(0.0);
+            if constexpr (par_k > 0) {
+                constexpr int m0 = static_cast<int>(MB::B.M[k][0]);
+                static_assert(double(m0) == MB::B.M[k][0], "integer basis");
+                m = macc<m0>(m, f0);
+                sfor<NP>([&](auto pI) {
+                    constexpr int pp = decltype(pI)::value;
+                    constexpr int mk = static_cast<int>(MB::B.M[k][2 * pp + 1]);
+                    static_assert(double(mk) == MB::B.M[k][2 * pp + 1], "integer basis");
+                    m = macc<mk>(m, P[pp]);
+                });
+                constexpr double A = MB::T.A[k];
+                if constexpr (A != 0.0) m = vfma(vsplat<V>(-A), e0, m);
+                sfor<DIM>([&](auto iI) {
+                    constexpr int i = decltype(iI)::value;
+                    sfor<DIM>([&](auto jI) {
+                        constexpr int jj = decltype(jI)::value;
+                        constexpr double c = MB::T.C[k][i][jj];
+                        if constexpr (c != 0.0) m = vfma(vsplat<V>(-0.5 * c / (cs2 * cs2)), vmul(u[i], v[jj]), m);
+                    });
+                });
+            } else {
+                sfor<NP>([&](auto pI) {
+                    constexpr int pp = decltype(pI)::value;
+                    constexpr int mk = static_cast<int>(MB::B.M[k][2 * pp + 1]);
+                    static_assert(double(mk) == MB::B.M[k][2 * pp + 1], "integer basis");
+                    m = macc<mk>(m, D[pp]);
+                });
+                sfor<DIM>([&](auto iI) {
+                    constexpr int i = decltype(iI)::value;
+                    constexpr double bc = MB::T.Bv[k][i];
+                    if constexpr (bc != 0.0) m = vfma(vsplat<V>(-bc / cs2), j[i], m);
+                });
+            }
+            constexpr double inv_norm = MB::B.inv_norm[k];
+            t[k] = vmul(dm[rc], vmul(vsplat<V>(inv_norm), m));
+        }
+    });
+}
+
+// f_b += sum_k M_kb t_k over the non-conserved moments, by opposite pairs:
+// f_b += E + O, f_b+1 += E - O with E from the even rows and O from the odd ones.
+template <int LAT, class V>
+__device__ __forceinline__ void mrt_apply(const V (&t)[Lattice<LAT>::Q], V (&f)[Lattice<LAT>::Q])
+{
+    using L = Lattice<LAT>;
+    using MB = Mrt<LAT>;
+    constexpr int Q = L::Q;
+    {
+        V e = vsplat<V>(0.0);
+        sfor<Q>([&](auto kI) {
+            constexpr int k = decltype(kI)::value;
+            if constexpr (MB::B.rate_class[k] != 0 && MB::T.parity[k] > 0)
+                e = macc<static_cast<int>(MB::B.M[k][0])>(e, t[k]);
+        });
+        f[0] = vadd(f[0], e);
+    }
+    sfor<(Q - 1) / 2>([&](auto pI) {
+        constexpr int b = 2 * decltype(pI)::value + 1;
+        V e = vsplat<V>(0.0), o = vsplat<V>(0.0);
+        sfor<Q>([&](auto kI) {
+            constexpr int k = decltype(kI)::value;
+            if constexpr (MB::B.rate_class[k] != 0) {
+                constexpr int mk = static_cast<int>(MB::B.M[k][b]);
+                if constexpr (MB::T.parity[k] > 0) e = macc<mk>(e, t[k]);
+                else o = macc<mk>(o, t[k]);
+            }
+        });
+        f[b] = vadd(f[b], vadd(e, o));
+        f[b + 1] = vadd(f[b + 1], vsub(e, o));
+    });
 }
 
 // ---- collision (Eqs. 3-4) --------------------------------------------------------
@@ -240,19 +398,23 @@ template <int LAT, int COLL, class Real>
 __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (&F)[3], const DevParams& p)
 {
     using L = Lattice<LAT>;
+    constexpr int NP = (L::Q - 1) / 2;
     constexpr bool kDev = std::is_same<Real, float>::value;  // deviation storage
     // Moments through the opposite pairs (b, b+1): sum f and sum (f_b - f_b+1) c_b.
     Real s = f[0], jx = Real(0), jy = Real(0), jz = Real(0);
-    sfor<(L::Q - 1) / 2>([&](auto kI) {
+    Real Pp[NP], Dp[NP];  // pair sums and differences (MRT)
+    sfor<NP>([&](auto kI) {
         constexpr int b = 1 + 2 * decltype(kI)::value;
         constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
-        s += f[b] + f[b + 1];
+        Pp[decltype(kI)::value] = f[b] + f[b + 1];
+        s += Pp[decltype(kI)::value];
         const Real d = f[b] - f[b + 1];
+        Dp[decltype(kI)::value] = d;
         if (cx != 0) jx += Real(cx) * d;
         if (cy != 0) jy += Real(cy) * d;
         if (cz != 0) jz += Real(cz) * d;
     });
-    const Real rho = kDev ? Real(p.rho_bar) + s : s;
+    const Real rho = kDev ? par<Real>(p.rho_bar, p.rho_bar_f) + s : s;
     const Real inv_rho = Real(1) / rho;
     const Real ux = (jx + Real(0.5) * F[0]) * inv_rho;
     const Real uy = (jy + Real(0.5) * F[1]) * inv_rho;
@@ -263,9 +425,20 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
     const Real half_inv_cs4 = Real(0.5 / (cs2 * cs2));
     const Real usq = (ux * ux + uy * uy + uz * uz) * Real(0.5 / cs2);
     const Real uF = ux * F[0] + uy * F[1] + uz * F[2];
-    const Real omega = Real(p.omega);
-    const Real pref = Real(p.pref);
-    if constexpr (COLL == 0) {
+    const Real omega = par<Real>(p.omega, p.omega_f);
+    const Real pref = par<Real>(p.pref, p.pref_f);
+    if constexpr (COLL == 0 || COLL == 1) {
+        // MRT: the moment-space correction is formed from the pre-collision state
+        Real t[L::Q];
+        if constexpr (COLL == 1) {
+            const Real jv[3] = {jx, jy, jz};
+            const Real uv3[3] = {ux, uy, uz};
+            const Real vv[3] = {jx - Real(0.5) * F[0], jy - Real(0.5) * F[1], jz - Real(0.5) * F[2]};
+            Real dm[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dm[c] = par<Real>(p.dmrt[c], p.dmrt_f[c]);
+            mrt_moments_g<LAT, Real>(f[0], Pp, Dp, kDev ? s : rho, jv, uv3, vv, dm, t);
+        }
         // omega feq_b + pref src_b regrouped (Eq. 4):
         //   w_b [ A0 + (c.u)(c.V) + c.P ],
         //   A0 = omega rho (1 - u.u/(2 cs2)) - pref u.F / cs2   (FP32: omega (rho - rho_bar) in
@@ -286,7 +459,7 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
             constexpr double w0 = L::T.w[0];
             f[0] = f[0] * om1 + Real(w0) * A0;
         }
-        sfor<(L::Q - 1) / 2>([&](auto kI) {
+        sfor<NP>([&](auto kI) {
             constexpr int b = 1 + 2 * decltype(kI)::value;
             constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
             static_assert(L::T.v[b + 1][0] == -cx && L::T.v[b + 1][1] == -cy && L::T.v[b + 1][2] == -cz,
@@ -299,50 +472,8 @@ __device__ __forceinline__ void collide(Real (&f)[Lattice<LAT>::Q], const Real (
             f[b] = f[b] * om1 + Real(wb) * (ev + cP);
             f[b + 1] = f[b + 1] * om1 + Real(wb) * (ev - cP);
         });
-    } else if constexpr (COLL == 1) {
-        // Moment space: f* = f + M^-1 [ -S (m - m_eq) + (I - S/2) M phi~ ],
-        // m_eq := M feq, M^-1 = M^T diag(1/|row|^2) (orthogonal rows).
-        using MB = Mrt<LAT>;
-        Real d[L::Q], src[L::Q];
-        sfor<L::Q>([&](auto bI) {
-            constexpr int b = decltype(bI)::value;
-            constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
-            constexpr double wb = L::T.w[b];
-            const Real w = Real(wb);
-            const Real cu = Real(cx) * ux + Real(cy) * uy + Real(cz) * uz;
-            const Real cF = Real(cx) * F[0] + Real(cy) * F[1] + Real(cz) * F[2];
-            const Real poly = cu * inv_cs2 + cu * cu * half_inv_cs4 - usq;
-            const Real feq = kDev ? w * (s + rho * poly) : rho * w * (Real(1) + poly);
-            d[b] = f[b] - feq;
-            src[b] = w * ((cF - uF) * inv_cs2 + cu * cF * inv_cs4);
-        });
-        Real t[L::Q];
-        sfor<L::Q>([&](auto kI) {
-            constexpr int k = decltype(kI)::value;
-            Real dm = Real(0), ms = Real(0);
-            sfor<L::Q>([&](auto bI) {
-                constexpr int b = decltype(bI)::value;
-                constexpr double m = MB::B.M[k][b];
-                if (m != 0.0) {
-                    dm += Real(m) * d[b];
-                    ms += Real(m) * src[b];
-                }
-            });
-            constexpr int rc = MB::B.rate_class[k];
-            constexpr double inv_norm = MB::B.inv_norm[k];
-            const Real sk = Real(p.rate[rc]);
-            t[k] = (ms * (Real(1) - Real(0.5) * sk) - sk * dm) * Real(inv_norm);
-        });
-        sfor<L::Q>([&](auto bI) {
-            constexpr int b = decltype(bI)::value;
-            Real acc = Real(0);
-            sfor<L::Q>([&](auto kI) {
-                constexpr int k = decltype(kI)::value;
-                constexpr double m = MB::B.M[k][b];
-                if (m != 0.0) acc += Real(m) * t[k];
-            });
-            f[b] = f[b] + acc;
-        });
+        if constexpr (COLL == 1) mrt_apply<LAT, Real>(t, f);
+        (void)half_inv_cs4;
     } else {
         // Exact-difference forcing with BGK (the scheme of the paper's runs, Sec. 3):
         //   f* = feq(rho, v) + (1 - omega) (f - feq(rho, u')),  u' = j / rho, v = u' + F / rho,
@@ -460,7 +591,7 @@ __global__ void __launch_bounds__(32 * TY * TZ)
     if (!active) return;
     const Real* tc = tile + ((tz + (D == 3 ? R : 0)) * SY + (ty + R)) * SX + (tx + kGhostX);
     Real F[3];
-    force_from<LAT, ORD, Real, SX, SY>(tc, p.G, F);
+    force_from<LAT, ORD, Real, SX, SY>(tc, par<Real>(p.G, p.G_f), F);
     collide<LAT, COLL>(f, F, p);
     const long long c = cell_of(p, x, y, z);
     sfor<L::Q>([&](auto bI) {
@@ -516,7 +647,7 @@ __device__ __forceinline__ int wrap_any(int i, int n)
 }
 
 template <int LAT, int ORD, class Real, int EX, int E, int NS>
-__device__ __forceinline__ void force_ring(const Real* ring, int m, int cx, int cy, double G, Real (&F)[3])
+__device__ __forceinline__ void force_ring(const Real* ring, int m, int cx, int cy, Real G, Real (&F)[3])
 {
     using L = Lattice<LAT>;
     using S = Stencil<L::D, ORD>;
@@ -536,7 +667,7 @@ __device__ __forceinline__ void force_ring(const Real* ring, int m, int cx, int 
         if (ey != 0) ay += Real(wt * ey) * d;
         if (ez != 0) az += Real(wt * ez) * d;
     });
-    const Real gp = -Real(G) * base[R][0];
+    const Real gp = -G * base[R][0];
     F[0] = gp * ax;
     F[1] = gp * ay;
     F[2] = gp * az;
@@ -727,7 +858,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                     gather_off<LAT, Real, RE>(P, ixo, mo, zero, fcur);
             }
             Real F[3];
-            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, p.G, F);
+            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, par<Real>(p.G, p.G_f), F);
             collide<LAT, COLL>(fcur, F, p);
             const int c = m * mscale + cell_xy;
             sfor<Q>([&](auto bI) {
@@ -832,7 +963,7 @@ __global__ void __launch_bounds__(NX * TY + (PROD ? 32 : 0), 1)
     bool ok = true;
     auto wait_stage = [&](int s) -> const Real* {
         const int slot = (s - base) % NSTG;
-        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        if (ok && !mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;  // after a timeout, stop waiting
         phase ^= 1u << slot;
         return stage + slot * STG;
     };
@@ -898,7 +1029,7 @@ __global__ void __launch_bounds__(NX * TY + (PROD ? 32 : 0), 1)
             for (; next <= last && next <= m + R + NSTG; ++next) issue(next);
         if (active) {
             Real F[3];
-            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, ty + R, p.G, F);
+            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, ty + R, par<Real>(p.G, p.G_f), F);
             collide<LAT, COLL>(fcur, F, p);
             const int c = m * plane + cell_xy;
             sfor<Q>([&](auto bI) {
@@ -1016,7 +1147,7 @@ __global__ void __launch_bounds__(NX * TY + 32, 1)
     long long consumed = 0;  // the same count in every thread
     auto wait_seq = [&](long long q) -> const Real* {
         const int slot = static_cast<int>(q % NSTG);
-        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        if (ok && !mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;  // after a timeout, stop waiting
         phase ^= 1u << slot;
         return stage + slot * STG;
     };
@@ -1080,7 +1211,7 @@ __global__ void __launch_bounds__(NX * TY + 32, 1)
             if (producer) issue_upto(consumed);
             if (active) {
                 Real F[3];
-                force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, ty + R, p.G, F);
+                force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, ty + R, par<Real>(p.G, p.G_f), F);
                 collide<LAT, COLL>(fcur, F, p);
                 const int c = m * plane + cell_xy;
                 sfor<Q>([&](auto bI) {
@@ -1178,7 +1309,7 @@ __global__ void __launch_bounds__(TX + 32, 1)
     auto stage_of = [&](int s) { return stage + ((s - base) % NSTG) * STG; };
     auto wait_stage = [&](int s) {
         const int slot = (s - base) % NSTG;
-        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        if (ok && !mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;  // after a timeout, stop waiting
         phase ^= 1u << slot;
     };
     // f of the cell at tile offset cx (-R .. TX + R - 1) from stage st (pull)
@@ -1231,7 +1362,7 @@ __global__ void __launch_bounds__(TX + 32, 1)
             Real f[Q];
             load_cell(stage_of(m), tid, f);
             Real F[3];
-            force_ring<LAT, ORD, Real, EX, EX, NS>(ring, m, tid + R, 0, p.G, F);
+            force_ring<LAT, ORD, Real, EX, EX, NS>(ring, m, tid + R, 0, par<Real>(p.G, p.G_f), F);
             collide<LAT, COLL>(f, F, p);
             const int c = m * p.nx + x0 + tid;
             sfor<Q>([&](auto bI) {
@@ -1379,7 +1510,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                 f[b] = fi[b * NT];
             });
             Real F[3];
-            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, p.G, F);
+            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, par<Real>(p.G, p.G_f), F);
             collide<LAT, COLL>(f, F, p);
             const int c = m * mscale + cell_xy;
             sfor<Q>([&](auto bI) {
@@ -1522,7 +1653,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                 f[b] = st[b * NT];
             });
             Real F[3];
-            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, p.G, F);
+            force_ring<LAT, ORD, Real, EX, E, NS>(ring, m, tx + R, (D == 3) ? ty + R : 0, par<Real>(p.G, p.G_f), F);
             collide<LAT, COLL>(f, F, p);
             const int c = m * mscale + cell_xy;
             sfor<Q>([&](auto bI) {
@@ -1572,33 +1703,49 @@ __device__ __forceinline__ float2 cdot2(float2 vx, float2 vy, float2 vz)
     return r;
 }
 
-template <int LAT>
-__device__ __forceinline__ void collide2_bgk(float2 (&f)[Lattice<LAT>::Q], const float2 (&F)[3], const DevParams& p)
+// Packed-pair collision: BGK (COLL = 0) or MRT (COLL = 1, the BGK update plus
+// the moment-space correction of mrt_moments_g / mrt_apply), both Guo-forced.
+template <int LAT, int COLL = 0>
+__device__ __forceinline__ void collide2(float2 (&f)[Lattice<LAT>::Q], const float2 (&F)[3], const DevParams& p)
 {
+    static_assert(COLL == 0 || COLL == 1, "packed pairs: BGK or MRT");
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
+    constexpr int NP = (Q - 1) / 2;
     float2 s = f[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
-    sfor<(Q - 1) / 2>([&](auto kI) {
-        constexpr int b = 1 + 2 * decltype(kI)::value;
+    float2 Pp[NP], Dp[NP];
+    sfor<NP>([&](auto kI) {
+        constexpr int k = decltype(kI)::value;
+        constexpr int b = 1 + 2 * k;
         constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
-        s = add2(s, add2(f[b], f[b + 1]));
+        Pp[k] = add2(f[b], f[b + 1]);
+        s = add2(s, Pp[k]);
         const float2 d = sub2(f[b], f[b + 1]);
+        Dp[k] = d;
         if (cx == 1) jx = add2(jx, d); else if (cx == -1) jx = sub2(jx, d); else if (cx != 0) jx = fma2(p2(float(cx)), d, jx);
         if (cy == 1) jy = add2(jy, d); else if (cy == -1) jy = sub2(jy, d); else if (cy != 0) jy = fma2(p2(float(cy)), d, jy);
         if (cz == 1) jz = add2(jz, d); else if (cz == -1) jz = sub2(jz, d); else if (cz != 0) jz = fma2(p2(float(cz)), d, jz);
     });
-    const float2 rho = add2(p2(float(p.rho_bar)), s);
+    const float2 rho = add2(p2(p.rho_bar_f), s);
     const float2 inv_rho = make_float2(1.f / rho.x, 1.f / rho.y);
     const float2 ux = mul2(fma2(p2(0.5f), F[0], jx), inv_rho);
     const float2 uy = mul2(fma2(p2(0.5f), F[1], jy), inv_rho);
     const float2 uz = mul2(fma2(p2(0.5f), F[2], jz), inv_rho);
     constexpr double cs2 = L::cs2;
     constexpr bool k3 = L::D == 3;  // 2-D: no z terms (u_z = F_z = 0)
+    float2 t[Q];
+    if constexpr (COLL == 1) {
+        const float2 jv[3] = {jx, jy, jz};
+        const float2 uv3[3] = {ux, uy, uz};
+        const float2 vv[3] = {fma2(p2(-0.5f), F[0], jx), fma2(p2(-0.5f), F[1], jy), fma2(p2(-0.5f), F[2], jz)};
+        const float2 dm[4] = {p2(p.dmrt_f[0]), p2(p.dmrt_f[1]), p2(p.dmrt_f[2]), p2(p.dmrt_f[3])};
+        mrt_moments_g<LAT, float2>(f[0], Pp, Dp, s, jv, uv3, vv, dm, t);
+    }
     const float2 usq = k3 ? mul2(fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))), p2(float(0.5 / cs2)))
                           : mul2(fma2(ux, ux, mul2(uy, uy)), p2(float(0.5 / cs2)));
     const float2 uF = k3 ? fma2(ux, F[0], fma2(uy, F[1], mul2(uz, F[2]))) : fma2(ux, F[0], mul2(uy, F[1]));
-    const float2 omega = p2(float(p.omega));
-    const float2 pref = p2(float(p.pref));
+    const float2 omega = p2(p.omega_f);
+    const float2 pref = p2(p.pref_f);
     const float2 orho = mul2(omega, rho);
     // A0 = omega s - omega rho usq - pref uF / cs2
     const float2 A0 = fma2(mul2(pref, p2(float(-1.0 / cs2))), uF, fma2(orho, sub2(p2(0.f), usq), mul2(omega, s)));
@@ -1610,12 +1757,12 @@ __device__ __forceinline__ void collide2_bgk(float2 (&f)[Lattice<LAT>::Q], const
     const float2 Vx = mul2(fma2(h, ux, mul2(pref, F[0])), ic4);
     const float2 Vy = mul2(fma2(h, uy, mul2(pref, F[1])), ic4);
     const float2 Vz = mul2(fma2(h, uz, mul2(pref, F[2])), ic4);
-    const float2 om1 = p2(float(1.0 - p.omega));
+    const float2 om1 = p2(p.om1_f);
     {
         constexpr double w0 = L::T.w[0];
         f[0] = fma2(f[0], om1, mul2(p2(float(w0)), A0));
     }
-    sfor<(Q - 1) / 2>([&](auto kI) {
+    sfor<NP>([&](auto kI) {
         constexpr int b = 1 + 2 * decltype(kI)::value;
         constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
         constexpr double wb = L::T.w[b];
@@ -1626,6 +1773,7 @@ __device__ __forceinline__ void collide2_bgk(float2 (&f)[Lattice<LAT>::Q], const
         f[b] = fma2(f[b], om1, mul2(p2(float(wb)), add2(ev, cP)));
         f[b + 1] = fma2(f[b + 1], om1, mul2(p2(float(wb)), sub2(ev, cP)));
     });
+    if constexpr (COLL == 1) mrt_apply<LAT, float2>(t, f);
 }
 
 // Packed-pair form of the persistent whole-row schedule (FP32 BGK): a compute
@@ -1637,8 +1785,8 @@ __device__ __forceinline__ void collide2_bgk(float2 (&f)[Lattice<LAT>::Q], const
 // compute warp issues the stage copies right after each barrier and then
 // computes.  With 12 compute warps that keeps three warps per SM sub-partition
 // (a 13th warp would cap every thread at 128 registers).
-template <int LAT, int ORD, int NX, int TY, int NSTG, bool PRODW = true>
-__global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
+template <int LAT, int ORD, int COLL, int NX, int TY, int NSTG, bool PRODW = true, int NXMAX = NX>
+__global__ void __launch_bounds__((NXMAX / 2 * TY + 31) / 32 * 32 + (PRODW ? 32 : 0), 1)
     k_onepass_rowp2(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, int zc, int nitems)
 {
     using L = Lattice<LAT>;
@@ -1646,23 +1794,32 @@ __global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
     constexpr int R = S::radius;
     constexpr int Q = L::Q;
     static_assert(L::D == 3 && R == 1 && L::reach == 1, "row staging is written for 3-D radius-1 stencils");
-    constexpr int NT = NX / 2 * TY;  // compute threads
+    // NX > 0: rows of NX cells (compile time); NX = 0: the domain's own row
+    // length p.nx (<= NXMAX, a multiple of 4), and the compute threads are
+    // rounded up to whole warps, the lanes past the last row pair idle.
     constexpr int EY = TY + 2 * R;
-    constexpr int EX = NX + 2 * R;
-    constexpr int E = EX * EY;
     constexpr int NS = 2 * R + 2;
-    constexpr int STG = Q * EY * NX;
-    static_assert(NT % 32 == 0 && NT + 32 <= 1024 && NSTG >= 2 * R && NSTG <= 32 && NX % 4 == 0, "block / stages");
-    __shared__ float ring[NS * E];
+    static_assert(NX > 0 ? (NX / 2 * TY) % 32 == 0 && NX / 2 * TY + 32 <= 1024 && NX % 4 == 0
+                         : (NXMAX / 2 * TY + 31) / 32 * 32 + 32 <= 1024 && NXMAX % 4 == 0,
+                  "block shape");
+    static_assert(NSTG >= 2 * R && NSTG <= 32, "stages");
+    const int nx = NX > 0 ? NX : p.nx;
+    const int half = nx / 2;
+    const int NT = NX > 0 ? NX / 2 * TY : (half * TY + 31) / 32 * 32;  // compute threads, whole warps
+    const int EX = nx + 2 * R;
+    const int E = EX * EY;
+    const int STG = Q * EY * nx;
+    __shared__ float ring_s[NX > 0 ? NS * (NX + 2 * R) * EY : 1];
     __shared__ alignas(8) unsigned long long bars[NSTG];
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     float* stage = reinterpret_cast<float*>(dyn_smem);  // [NSTG][STG]
+    float* ring = NX > 0 ? ring_s : stage + NSTG * STG;  // [NS][E]
 
     const int nty = (p.ny + TY - 1) / TY;
     const int nm = p.nz;
-    const int plane = NX * p.ny;
+    const int plane = nx * p.ny;
     const int tid = threadIdx.x;
-    const int tp = tid % (NX / 2), ty = tid / (NX / 2);  // pair index along x, row in the tile
+    const int tp = tid % half, ty = tid / half;  // pair index along x, row in the tile (ty >= TY: idle lane)
     const int x0 = 2 * tp;                               // first cell of the pair
     const int lane = tid & 31;
     const bool producer = PRODW && tid >= NT;
@@ -1705,13 +1862,13 @@ __global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
         if (lane < Q) {
             fence_proxy_async_smem();
             const float* pl = src_b + static_cast<long long>(wrap_any(p_next - cbz, nm)) * plane;
-            uint32_t dst = smem_u32(stage + slot * STG + lane * (EY * NX));
+            uint32_t dst = smem_u32(stage + slot * STG + lane * (EY * nx));
             int y = p_y0 - R - cby, left = EY;
             while (left > 0) {
                 const int yw = wrap_any(y, p.ny);
                 const int n = (p.ny - yw < left) ? p.ny - yw : left;
-                bulk_g2s(dst, pl + static_cast<long long>(yw) * NX, static_cast<uint32_t>(n * NX * sizeof(float)), bar);
-                dst += static_cast<uint32_t>(n * NX * sizeof(float));
+                bulk_g2s(dst, pl + static_cast<long long>(yw) * nx, static_cast<uint32_t>(n * nx * sizeof(float)), bar);
+                dst += static_cast<uint32_t>(n * nx * sizeof(float));
                 y += n;
                 left -= n;
             }
@@ -1732,19 +1889,19 @@ __global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
     long long consumed = 0;
     auto wait_seq = [&](long long q) -> const float* {
         const int slot = static_cast<int>(q % NSTG);
-        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        if (ok && !mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;  // after a timeout, stop waiting
         phase ^= 1u << slot;
         return stage + slot * STG;
     };
     // pull columns of the pair for c_x = +1 (x - 1) and c_x = -1 (x + 1), periodic
-    const int xl = (x0 == 0) ? NX - 1 : x0 - 1;        // left of the first cell
-    const int xr = (x0 + 2 == NX) ? 0 : x0 + 2;        // right of the second cell
+    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;        // left of the first cell
+    const int xr = (x0 + 2 == nx) ? 0 : x0 + 2;        // right of the second cell
     auto load_pair = [&](const float* st, int fy, float2 (&f)[Q]) {
-        const float* r = st + fy * NX;
+        const float* r = st + fy * nx;
         sfor<Q>([&](auto bI) {
             constexpr int b = decltype(bI)::value;
             constexpr int vx = L::T.v[b][0];
-            const float* rb = r + b * (EY * NX);
+            const float* rb = r + b * (EY * nx);
             if (vx == 0)
                 f[b] = *reinterpret_cast<const float2*>(rb + x0);
             else if (vx > 0)
@@ -1764,11 +1921,12 @@ __global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
         float* row = dst + fy * EX;
         row[x0 + R] = v.x;
         row[x0 + 1 + R] = v.y;
-        if (x0 == 0) row[NX + R] = v.x;          // wrapped column right of the row
-        if (x0 + 2 == NX) row[0] = v.y;          // wrapped column left of the row
+        if (x0 == 0) row[nx + R] = v.x;          // wrapped column right of the row
+        if (x0 + 2 == nx) row[0] = v.y;          // wrapped column left of the row
     };
     auto psi_slab = [&](int s, long long q) {
         const float* st = wait_seq(q);
+        if (NX == 0 && ty >= TY) return;  // idle lane: keeps the barrier phases only
         float* dst = ring + ring_slot(s, NS) * E;
         load_pair(st, ty + R, fnxt);
         put_psi2(dst, ty + R, rho_psi2(fnxt));
@@ -1792,8 +1950,8 @@ __global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
         for (int b = 0; b < Q; ++b) fcur[b] = fnxt[b];
         __syncthreads();
         if (issuer) issue_upto(consumed);
-        const bool active = !producer && (y0 + ty) < p.ny;
-        const int cell_xy = (y0 + ty) * NX + x0;
+        const bool active = !producer && ty < TY && (y0 + ty) < p.ny;
+        const int cell_xy = (y0 + ty) * nx + x0;
         for (int m = m0; m < m1; ++m) {
             if (!producer) psi_slab(m + R, consumed);
             ++consumed;
@@ -1816,9 +1974,9 @@ __global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
                     if (ey != 0) ay = fma2(p2(float(wt * ey)), d, ay);
                     if (ez != 0) az = fma2(p2(float(wt * ez)), d, az);
                 });
-                const float2 gp = mul2(p2(float(-p.G)), make_float2(base[R][0], base[R][1]));
+                const float2 gp = mul2(p2(-p.G_f), make_float2(base[R][0], base[R][1]));
                 const float2 F[3] = {mul2(gp, ax), mul2(gp, ay), mul2(gp, az)};
-                collide2_bgk<LAT>(fcur, F, p);
+                collide2<LAT, COLL>(fcur, F, p);
                 const int c = m * plane + cell_xy;
                 sfor<Q>([&](auto bI) {
                     constexpr int b = decltype(bI)::value;
@@ -1839,7 +1997,7 @@ __global__ void __launch_bounds__(NX / 2 * TY + (PRODW ? 32 : 0), 1)
 // 8-byte load per pair, psi, the force and the collision run on float2 pairs
 // with the packed FP32 instructions, and every store is one 8-byte store.
 // Staging, stage reuse and the producer warp are those of k_onepass_seg.
-template <int LAT, int ORD, int TX, int ZC, int NSTG>
+template <int LAT, int ORD, int COLL, int TX, int ZC, int NSTG>
 __global__ void __launch_bounds__(TX / 2 + 32, 1)
     k_onepass_seg2(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, int ntx)
 {
@@ -1914,7 +2072,7 @@ __global__ void __launch_bounds__(TX / 2 + 32, 1)
     auto stage_of = [&](int s) { return stage + ((s - base) % NSTG) * STG; };
     auto wait_stage = [&](int s) {
         const int slot = (s - base) % NSTG;
-        if (!mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;
+        if (ok && !mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;  // after a timeout, stop waiting
         phase ^= 1u << slot;
     };
     // f of the cell at tile offset cx (-R .. TX + R - 1) from stage st (pull)
@@ -1997,9 +2155,9 @@ __global__ void __launch_bounds__(TX / 2 + 32, 1)
                 if (ex != 0) ax = fma2(p2(float(wt * ex)), d, ax);
                 if (ey != 0) ay = fma2(p2(float(wt * ey)), d, ay);
             });
-            const float2 gp = mul2(p2(float(-p.G)), make_float2(rowp[R][0], rowp[R][1]));
+            const float2 gp = mul2(p2(-p.G_f), make_float2(rowp[R][0], rowp[R][1]));
             const float2 F[3] = {mul2(gp, ax), mul2(gp, ay), p2(0.f)};
-            collide2_bgk<LAT>(f, F, p);
+            collide2<LAT, COLL>(f, F, p);
             const int c = m * p.nx + x0 + cx0;
             sfor<Q>([&](auto bI) {
                 constexpr int b = decltype(bI)::value;
@@ -2156,9 +2314,9 @@ __global__ void __launch_bounds__(TX2 * TY, MINB)
                 if (ey != 0) ay = fma2(p2(float(wt * ey)), d, ay);
                 if (ez != 0) az = fma2(p2(float(wt * ez)), d, az);
             });
-            const float2 gp = mul2(p2(float(-p.G)), make_float2(base[R][0], base[R][1]));
+            const float2 gp = mul2(p2(-p.G_f), make_float2(base[R][0], base[R][1]));
             const float2 F[3] = {mul2(gp, ax), mul2(gp, ay), mul2(gp, az)};
-            collide2_bgk<LAT>(fcur, F, p);
+            collide2<LAT, 0>(fcur, F, p);
             const int c = m * mscale + cell_xy;
             sfor<Q>([&](auto bI) {
                 constexpr int b = decltype(bI)::value;
@@ -2258,7 +2416,7 @@ __device__ __forceinline__ void cell_force_f32(const float* __restrict__ psi, co
         if (ey != 0) ay = fmaf(wt * ey, d, ay);
         if (ez != 0) az = fmaf(wt * ez, d, az);
     });
-    const float gp = -static_cast<float>(p.G) * c0[0];
+    const float gp = -p.G_f * c0[0];
     F[0] = gp * ax;
     F[1] = gp * ay;
     F[2] = gp * az;
@@ -2567,11 +2725,11 @@ inline int rowp_chunk(int nz, int nty, int nsm)
     return zc;
 }
 
-template <int LAT, int ORD, int NX, int TY, int NSTG, bool PRODW = true>
+template <int LAT, int ORD, int COLL, int NX, int TY, int NSTG, bool PRODW = true>
 cudaError_t launch_onepass_rowp2(const LaunchArgs& a, cudaStream_t s)
 {
     constexpr size_t dyn = sizeof(float) * NSTG * Lattice<LAT>::Q * (TY + 2) * NX;
-    auto kern = &k_onepass_rowp2<LAT, ORD, NX, TY, NSTG, PRODW>;
+    auto kern = &k_onepass_rowp2<LAT, ORD, COLL, NX, TY, NSTG, PRODW>;
     if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     if (a.p.nx != NX) return cudaErrorInvalidValue;
     const int nty = (a.p.ny + TY - 1) / TY;
@@ -2583,6 +2741,37 @@ cudaError_t launch_onepass_rowp2(const LaunchArgs& a, cudaStream_t s)
     const int grid = nitems < nsm ? nitems : nsm;
     const auto P = make_pops<float, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
     kern<<<grid, NX / 2 * TY + (PRODW ? 32 : 0), dyn, s>>>(P, a.p, zc, nitems);
+    return cudaGetLastError();
+}
+
+// Whole-row packed-pair schedule for any row length nx <= NXMAX that is a
+// multiple of 4 (16-byte rows for the bulk copies): the kernel reads nx from
+// the domain, the psi ring moves into dynamic shared memory after the stages,
+// and the compute threads are rounded up to whole warps.
+template <int LAT, int ORD, int COLL, int NXMAX, int TY, int NSTG, bool PRODW>
+cudaError_t launch_onepass_rowp2w(const LaunchArgs& a, cudaStream_t s)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    constexpr int R = Stencil<3, ORD>::radius;
+    constexpr int EY = TY + 2 * R;
+    constexpr int NS = 2 * R + 2;
+    auto dyn_of = [](int nx) {
+        return sizeof(float) * (static_cast<size_t>(NSTG) * Q * EY * nx + static_cast<size_t>(NS) * (nx + 2 * R) * EY);
+    };
+    auto kern = &k_onepass_rowp2<LAT, ORD, COLL, 0, TY, NSTG, PRODW, NXMAX>;
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn_of(NXMAX)); e != cudaSuccess) return e;
+    const int nx = a.p.nx;
+    if (nx % 4 != 0 || nx < 8 || nx > NXMAX) return cudaErrorInvalidValue;
+    const int nty = (a.p.ny + TY - 1) / TY;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int zc = rowp_chunk(a.p.nz, nty, nsm);
+    const int nitems = nty * ((a.p.nz + zc - 1) / zc);
+    const int grid = nitems < nsm ? nitems : nsm;
+    const int threads = (nx / 2 * TY + 31) / 32 * 32 + (PRODW ? 32 : 0);
+    const auto P = make_pops<float, Q>(a.fin, a.fout, a.p.N);
+    kern<<<grid, threads, dyn_of(nx), s>>>(P, a.p, zc, nitems);
     return cudaGetLastError();
 }
 
@@ -2653,11 +2842,11 @@ cudaError_t launch_onepass_seg(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int LAT, int ORD, int TX, int ZC, int NSTG>
+template <int LAT, int ORD, int COLL, int TX, int ZC, int NSTG>
 cudaError_t launch_onepass_seg2(const LaunchArgs& a, cudaStream_t s)
 {
     constexpr size_t dyn = sizeof(float) * NSTG * Lattice<LAT>::Q * (TX + 8);
-    auto kern = &k_onepass_seg2<LAT, ORD, TX, ZC, NSTG>;
+    auto kern = &k_onepass_seg2<LAT, ORD, COLL, TX, ZC, NSTG>;
     if (cudaError_t e = ensure_dyn_smem(kern, dyn); e != cudaSuccess) return e;
     if (a.p.nx % 4 != 0) return cudaErrorInvalidValue;
     const int ntx = (a.p.nx + TX - 1) / TX;
@@ -2787,29 +2976,33 @@ cudaError_t launch_rho_of_f(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The one-pass variants offered to the autotuner for (LAT, ORD, COLL, Real):
+// tile TX x TY (2-D: TX), chunk of ZC slabs, at least MINB resident blocks per
+// SM (a register cap).  Built at compile time, so a list longer than the
+// schedule table is a build error rather than a silently dropped variant.
+struct VariantList {
+    int n;
+    bool overflow;
+    StepVariant v[kMaxVariants];
+};
+
 template <int LAT, int ORD, int COLL, class Real>
-KernelSet make_set()
+constexpr VariantList make_variants()
 {
     constexpr bool k3 = Lattice<LAT>::D == 3;
-    constexpr int TY = k3 ? 4 : 8;
-    constexpr int TZ = k3 ? 2 : 1;
-    KernelSet k{};
-    k.tile_x = 32;
-    k.tile_y = TY;
-    k.tile_z = TZ;
-    k.psi = &launch_psi<LAT, Real>;
-    k.fused = &launch_fused<LAT, ORD, COLL, Real, TY, TZ>;
-    // One-pass variants timed by the autotuner: tile TX x TY (2-D: TX), chunk of
-    // ZC slabs, at least MINB resident blocks per SM (a register cap).
-    k.n_onepass = 0;
+    VariantList k{};
     auto add = [&k](const char* name, cudaError_t (*fn)(const LaunchArgs&, cudaStream_t), int nx_mult = 1,
-                    int nx_exact = 0) {
-        if (k.n_onepass >= kMaxVariants) return;  // table full: later variants are not offered
-        k.onepass[k.n_onepass].name = name;
-        k.onepass[k.n_onepass].fn = fn;
-        k.onepass[k.n_onepass].nx_multiple = nx_mult;
-        k.onepass[k.n_onepass].nx_exact = nx_exact;
-        ++k.n_onepass;
+                    int nx_exact = 0, int nx_max = 0) {
+        if (k.n >= kMaxVariants) {
+            k.overflow = true;
+            return;
+        }
+        k.v[k.n].name = name;
+        k.v[k.n].fn = fn;
+        k.v[k.n].nx_multiple = nx_mult;
+        k.v[k.n].nx_exact = nx_exact;
+        k.v[k.n].nx_max = nx_max;
+        ++k.n;
     };
     constexpr bool r1 = Stencil<Lattice<LAT>::D, ORD>::radius == 1;
     constexpr bool hot = COLL == 0 && std::is_same<Real, float>::value;
@@ -2818,9 +3011,7 @@ KernelSet make_set()
         if constexpr (hot) {
             add("onepass_32x8_z16_b4_smem", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 4, 2>);
             add("onepass_32x8_z16_b3_smem", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 3, 2>);
-            if constexpr (r1) {
-                add("onepass_32x8_z16_b3_reg", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 3, 1>);
-                }
+            if constexpr (r1) add("onepass_32x8_z16_b3_reg", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 3, 1>);
             add("onepass_32x8_z16_b4_regather", &launch_onepass<LAT, ORD, COLL, Real, 32, 8, 16, 4, 0>);
             add("onepass_async_32x8_z16_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 32, 8, 16, 2>);
             add("onepass_async_32x8_z32_b2", &launch_onepass_async<LAT, ORD, COLL, Real, 32, 8, 32, 2>);
@@ -2832,9 +3023,12 @@ KernelSet make_set()
                 add("onepass_row256x2_zauto_s2_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 0, 2, 1>, 1, 256);
                 add("onepass_row256x2_zauto_s2_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 256, 2, 0, 2, 2>, 1, 256);
                 add("onepass_rowp256x2_s2", &launch_onepass_rowp<LAT, ORD, COLL, Real, 256, 2, 2>, 1, 256);
-                add("onepass_rowp2_256x2_s2", &launch_onepass_rowp2<LAT, ORD, 256, 2, 2>, 1, 256);
-                add("onepass_rowp2_256x3_s2", &launch_onepass_rowp2<LAT, ORD, 256, 3, 2>, 1, 256);
-                add("onepass_rowp2_256x3_s2_np", &launch_onepass_rowp2<LAT, ORD, 256, 3, 2, false>, 1, 256);
+                add("onepass_rowp2_256x2_s2", &launch_onepass_rowp2<LAT, ORD, 0, 256, 2, 2>, 1, 256);
+                add("onepass_rowp2_256x3_s2", &launch_onepass_rowp2<LAT, ORD, 0, 256, 3, 2>, 1, 256);
+                add("onepass_rowp2_256x3_s2_np", &launch_onepass_rowp2<LAT, ORD, 0, 256, 3, 2, false>, 1, 256);
+                add("onepass_rowp2_w256x3_s2_np", &launch_onepass_rowp2w<LAT, ORD, 0, 256, 3, 2, false>, 4, 0, 256);
+                add("onepass_rowp2_w344x2_s2", &launch_onepass_rowp2w<LAT, ORD, 0, 344, 2, 2, true>, 4, 0, 344);
+                add("onepass_rowp2_w456x1_s2", &launch_onepass_rowp2w<LAT, ORD, 0, 456, 1, 2, true>, 4, 0, 456);
                 add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 0>, 1, 128);
                 add("onepass_row128x4_z32_s3_prod", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 1>, 1, 128);
                 add("onepass_row128x4_zauto_s3_prod_cs", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 0, 3, 2>, 1, 128);
@@ -2850,8 +3044,15 @@ KernelSet make_set()
             add("onepass_la_32x8_z16_b2", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 2, 1>);
             add("onepass_lai_32x8_z16_b3", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 3, 0>);
             add("onepass_x2_64x8_z16_b2_smem", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 2>, 2);
-            if constexpr (r1) {
-            }
+        }
+        // MRT in FP32: the packed-pair whole-row kernels (nx = 256)
+        if constexpr (COLL == 1 && std::is_same<Real, float>::value && r1) {
+            add("onepass_rowp2_256x3_s2_np", &launch_onepass_rowp2<LAT, ORD, 1, 256, 3, 2, false>, 1, 256);
+            add("onepass_rowp2_256x2_s2", &launch_onepass_rowp2<LAT, ORD, 1, 256, 2, 2>, 1, 256);
+            add("onepass_rowp2_256x3_s2", &launch_onepass_rowp2<LAT, ORD, 1, 256, 3, 2>, 1, 256);
+            add("onepass_rowp2_w256x3_s2_np", &launch_onepass_rowp2w<LAT, ORD, 1, 256, 3, 2, false>, 4, 0, 256);
+            add("onepass_rowp2_w344x2_s2", &launch_onepass_rowp2w<LAT, ORD, 1, 344, 2, 2, true>, 4, 0, 344);
+            add("onepass_rowp2_w456x1_s2", &launch_onepass_rowp2w<LAT, ORD, 1, 456, 1, 2, true>, 4, 0, 456);
         }
     } else {
         add("onepass_128_z16_b2_smem", &launch_onepass<LAT, ORD, COLL, Real, 128, 1, 16, 2, 2>);
@@ -2865,13 +3066,37 @@ KernelSet make_set()
                 add("onepass_seg256_z64_s6", &launch_onepass_seg<LAT, ORD, COLL, Real, 256, 64, 6>, 4);
                 add("onepass_seg128_z64_s8", &launch_onepass_seg<LAT, ORD, COLL, Real, 128, 64, 8>, 4);
                 add("onepass_seg512_z64_s6", &launch_onepass_seg<LAT, ORD, COLL, Real, 512, 64, 6>, 4);
-                add("onepass_seg2_256_z64_s6", &launch_onepass_seg2<LAT, ORD, 256, 64, 6>, 4);
-                add("onepass_seg2_512_z64_s6", &launch_onepass_seg2<LAT, ORD, 512, 64, 6>, 4);
+                add("onepass_seg2_256_z64_s6", &launch_onepass_seg2<LAT, ORD, 0, 256, 64, 6>, 4);
+                add("onepass_seg2_512_z64_s6", &launch_onepass_seg2<LAT, ORD, 0, 512, 64, 6>, 4);
                 if constexpr (Stencil<2, ORD>::radius <= 2)
-                    add("onepass_seg2_512_z64_s4", &launch_onepass_seg2<LAT, ORD, 512, 64, 4>, 4);
+                    add("onepass_seg2_512_z64_s4", &launch_onepass_seg2<LAT, ORD, 0, 512, 64, 4>, 4);
             }
         }
+        // MRT in FP32 (D2Q9): the packed-pair segment kernels
+        if constexpr (COLL == 1 && std::is_same<Real, float>::value && Lattice<LAT>::reach == 1) {
+            add("onepass_seg2_256_z64_s6", &launch_onepass_seg2<LAT, ORD, 1, 256, 64, 6>, 4);
+            add("onepass_seg2_512_z64_s6", &launch_onepass_seg2<LAT, ORD, 1, 512, 64, 6>, 4);
+        }
     }
+    return k;
+}
+
+template <int LAT, int ORD, int COLL, class Real>
+KernelSet make_set()
+{
+    constexpr bool k3 = Lattice<LAT>::D == 3;
+    constexpr int TY = k3 ? 4 : 8;
+    constexpr int TZ = k3 ? 2 : 1;
+    KernelSet k{};
+    k.tile_x = 32;
+    k.tile_y = TY;
+    k.tile_z = TZ;
+    k.psi = &launch_psi<LAT, Real>;
+    k.fused = &launch_fused<LAT, ORD, COLL, Real, TY, TZ>;
+    constexpr VariantList V = make_variants<LAT, ORD, COLL, Real>();
+    static_assert(!V.overflow, "more one-pass variants than the schedule table holds: raise kMaxVariants");
+    k.n_onepass = V.n;
+    for (int i = 0; i < V.n; ++i) k.onepass[i] = V.v[i];
     k.obs = &launch_obs<LAT, ORD, Real>;
     k.probe = &launch_probe<LAT, Real>;
     k.fields = &launch_fields<LAT, ORD, Real>;

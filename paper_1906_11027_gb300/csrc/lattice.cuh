@@ -225,8 +225,50 @@ constexpr MrtBasis make_mrt()
     return m;
 }
 
+// Moments of the equilibrium's building blocks for each basis row k:
+//   A_k = sum_b M_kb w_b,  B_ki = sum_b M_kb w_b c_bi,  C_kij = sum_b M_kb w_b c_bi c_bj,
+// so that for feq_b = w_b rho (1 + c.u/cs2 + (c.u)^2/(2 cs4) - u.u/(2 cs2)) and Guo's
+// source src_b = w_b [(c - u)/cs2 + (c.u) c/cs4].F (Eq. 4):
+//   m_k(feq) = rho [A_k + B_k.u/cs2 + u.C_k.u/(2 cs4) - A_k u.u/(2 cs2)],
+//   m_k(src) = B_k.F/cs2 - A_k u.F/cs2 + u.C_k.F/cs4.
+// parity[k] = +1 if row k is even under c -> -c (M_kb equal on opposite
+// velocities), -1 if odd (opposite values, zero on the rest velocity).
+struct MrtMoments {
+    double A[25];
+    double Bv[25][3];
+    double C[25][3][3];
+    int parity[25];
+};
+
+template <int ID>
+constexpr MrtMoments make_mrt_moments()
+{
+    MrtMoments t{};
+    constexpr VecSet T = Lattice<ID>::T;
+    constexpr int Q = Lattice<ID>::Q;
+    const MrtBasis m = make_mrt<ID>();
+    for (int k = 0; k < Q; ++k) {
+        for (int b = 0; b < Q; ++b) {
+            const double mw = m.M[k][b] * T.w[b];
+            t.A[k] += mw;
+            for (int i = 0; i < 3; ++i) {
+                t.Bv[k][i] += mw * T.v[b][i];
+                for (int j = 0; j < 3; ++j) t.C[k][i][j] += mw * T.v[b][i] * T.v[b][j];
+            }
+        }
+        bool even = true, odd = (m.M[k][0] == 0.0);
+        for (int b = 1; b + 1 < Q; b += 2) {
+            even = even && (m.M[k][b] == m.M[k][b + 1]);
+            odd = odd && (m.M[k][b] == -m.M[k][b + 1]);
+        }
+        t.parity[k] = even ? 1 : (odd ? -1 : 0);
+    }
+    return t;
+}
+
 template <int ID> struct Mrt {
     static constexpr MrtBasis B = make_mrt<ID>();
+    static constexpr MrtMoments T = make_mrt_moments<ID>();
 };
 
 }  // namespace lbm

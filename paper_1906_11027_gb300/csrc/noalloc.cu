@@ -39,7 +39,10 @@ constexpr int kNoAllocResult = kNoAllocBlocks * kNoAllocWidth;  // offset of the
 static __device__ __align__(256) double g_moments_scratch[kNoAllocBlocks * kNoAllocWidth + 8];
 
 // One partial per block: sums over its 1024 cells of rho and sum_b f_b c_b,
-// reduced in a fixed order (warp shuffles, then warps in index order).
+// reduced in a fixed order (warp shuffles, then warps in index order).  The
+// buffer is summed as stored, A_b[i] for every direction b and cell i, with
+// coalesced loads: the totals over the whole periodic box are the same as over
+// the pulled populations f_b(x) = A_b(x - c_b), a permutation of the cells.
 template <int LAT, class Real>
 __global__ void __launch_bounds__(256) k_moments_partials(const Real* __restrict__ A, DevParams p,
                                                           double* __restrict__ scratch)
@@ -49,17 +52,11 @@ __global__ void __launch_bounds__(256) k_moments_partials(const Real* __restrict
     for (int k = 0; k < kNoAllocCellsPerBlock / 256; ++k) {
         const long long i = static_cast<long long>(blockIdx.x) * kNoAllocCellsPerBlock + k * 256 + threadIdx.x;
         if (i >= p.N) break;
-        const int x = static_cast<int>(i % p.nx);
-        const long long r = i / p.nx;
-        const int y = static_cast<int>(r % p.ny);
-        const int z = static_cast<int>(r / p.ny);
-        Real f[L::Q];
-        gather<LAT>(A, p, x, y, z, f);
         double s = 0.0, j[3] = {0.0, 0.0, 0.0};
         sfor<L::Q>([&](auto bI) {
             constexpr int b = decltype(bI)::value;
             constexpr int cx = L::T.v[b][0], cy = L::T.v[b][1], cz = L::T.v[b][2];
-            const double fb = static_cast<double>(f[b]);
+            const double fb = static_cast<double>(A[static_cast<long long>(b) * p.N + i]);
             s += fb;
             j[0] += fb * cx;
             j[1] += fb * cy;

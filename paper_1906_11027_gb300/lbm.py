@@ -119,6 +119,8 @@ _SIGNATURES = {
     "lbm_mlp_save": (_I, [_P, ctypes.c_char_p]),
     "lbm_mlp_load": (_I, [ctypes.POINTER(_P), ctypes.c_char_p]),
     "lbm_init_droplet_learned": (_I, [_P, _P, _D, _D, _D, _D, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "lbm_reference_density": (_I, [_P, ctypes.POINTER(_D)]),
+    "lbm_diag_wait_timeout": (_I, [_P]),
     "lbm_strerror": (ctypes.c_char_p, [_I]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -482,6 +484,17 @@ def lbm_init_droplet_learned(ctx, mlp, R, rho_l, rho_g, width):
     _check(load().lbm_init_droplet_learned(ctx, mlp.h, R, rho_l, rho_g, width, ctypes.byref(fb),
                                            ctypes.byref(reff)), "lbm_init_droplet_learned")
     return bool(fb.value), reff.value
+
+
+def lbm_reference_density(ctx) -> float:
+    v = _D()
+    _check(load().lbm_reference_density(ctx, ctypes.byref(v)), "lbm_reference_density")
+    return v.value
+
+
+def lbm_diag_wait_timeout(ctx) -> int:
+    """Runs the bounded-wait probe; returns the library's code (LBM_ETIMEOUT expected)."""
+    return int(_lib.lbm_diag_wait_timeout(ctx))
 
 
 def lbm_strerror(code: int) -> str:

@@ -1,7 +1,7 @@
 """Small profiling driver: one domain, a few directly launched steps, so that a
 profiler can capture individual kernels.
 
-    python -m paper_1906_11027_gb300.profile_case --lattice d3q19 --n 128 --steps 6 \
+    python -m paper_1906_11027_gb300.profile_case --lattice d3q19 --n 128 [--nz 32] --steps 6 \
         [--precision fp32|fp64] [--stencil 4] [--coll bgk|mrt] [--path auto|two|one] [--schedule NAME]
 """
 import argparse
@@ -21,6 +21,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--lattice", choices=sorted(LATTICES), default="d3q19")
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--nz", type=int, default=0, help="3-D: number of z planes (default n)")
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--stencil", type=int, default=0)
@@ -29,7 +30,7 @@ def main():
     ap.add_argument("--schedule", default=None, help="pin a schedule by name (lbm_schedule_report)")
     a = ap.parse_args()
     lat = LATTICES[a.lattice]
-    nz = a.n if lat == lbm.LBM_D3Q19 else 1
+    nz = (a.nz or a.n) if lat == lbm.LBM_D3Q19 else 1
     dom = lbm.Domain(a.n, a.n, nz, lattice=lat, stencil=a.stencil,
                      precision=lbm.LBM_FP32_SHIFTED if a.precision == "fp32" else lbm.LBM_FP64,
                      collision=COLLS[a.coll], path=PATHS[a.path])

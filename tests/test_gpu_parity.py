@@ -291,6 +291,31 @@ def test_full_size_d3q19_256_fp32_against_oracle(lbm):
     assert dom.observables()["mass"] == pytest.approx(m0, rel=1e-6)
 
 
+@pytest.mark.parametrize("coll", [0, 1])
+def test_full_size_headline_schedule_populations_against_oracle(lbm, coll):
+    """The benchmark's schedule at the benchmark's size, populations compared
+    cell by cell: D3Q19, FP32 deviations, 256^3, psi = 1 - exp(-rho), G = -5,
+    4th-order stencil, droplet R = 40, with the packed-pair whole-row kernel
+    (three rows per item, no producer warp) pinned, BGK and MRT.  At this size
+    every block walks several items, so the copy sequence runs on across item
+    boundaries.  After three steps every population lies within 2e-6 of the
+    largest (FP32 storage of deviations of size ~0.3, rounded at 2^-24)."""
+    n = 256
+    dom = lbm.Domain(n, n, n, lattice=lbm.LBM_D3Q19, stencil=4, precision=1, G=-5.0, tau=1.0, collision=coll)
+    dom.set_schedule("onepass_rowp2_256x3_s2_np")
+    dom.init_droplet(2.0, 0.15, 40.0, 2.0)
+    dom.step(3)
+    f_gpu = dom.get_f()
+    dom.close()
+    ref = oracle.Sim(oracle.D3Q19, n, n, n, stencil=4, G=-5.0, tau=1.0, coll=coll)
+    ref.init_droplet(2.0, 0.15, 40.0, 2.0)
+    ref.step(3)
+    f_ref = ref.get_f()
+    del ref
+    err = np.abs(f_gpu - f_ref).max() / np.abs(f_ref).max()
+    assert err <= 2e-6, err
+
+
 @pytest.mark.parametrize("lattice,shape,stencil,coll,precision", [
     (0, (1, 29, 37), 10, 1, 0),
     (0, (1, 40, 300), 4, 0, 1),
@@ -323,32 +348,41 @@ def test_one_pass_ragged_3d_against_oracle(lbm):
     assert rel_max(dom.get_f(), ref.get_f()) <= 1e-12
 
 
-@pytest.mark.parametrize("lattice,shape,stencil,precision", [
-    (1, (40, 24, 70), 4, 1),    # 3-D FP32 hot path: every compiled variant
-    (1, (12, 10, 128), 4, 1),   # nx = 128 and 256: the whole-row staged variants too
-    (1, (9, 10, 256), 4, 1),
-    (1, (21, 19, 37), 6, 1),
-    (1, (20, 16, 33), 4, 0),
-    (0, (1, 45, 300), 4, 1),
-    (0, (1, 70, 520), 8, 1),    # radius-2 stencil: every segment variant, ragged tiles and chunks
-    (0, (1, 37, 260), 10, 1),   # radius 3, the widest halo the segment staging takes
-    (0, (1, 33, 70), 10, 0),
-    (3, (1, 37, 150), 0, 1),
+@pytest.mark.parametrize("lattice,shape,stencil,precision,coll", [
+    (1, (40, 24, 70), 4, 1, 0),    # 3-D FP32 hot path: every compiled variant
+    (1, (12, 10, 128), 4, 1, 0),   # nx = 128 and 256: the whole-row staged variants too
+    (1, (9, 10, 256), 4, 1, 0),
+    (1, (9, 10, 256), 4, 1, 1),    # MRT on the packed-pair whole-row kernels
+    (1, (9, 10, 200), 4, 1, 0),    # runtime row lengths: 200 (three rows per item), ragged rows
+    (1, (7, 11, 300), 4, 1, 1),    # 300 (two rows per item), MRT
+    (1, (6, 5, 420), 4, 1, 0),     # 420 (one row per item)
+    (1, (21, 19, 37), 6, 1, 0),
+    (1, (20, 16, 33), 4, 0, 0),
+    (1, (13, 11, 256), 4, 0, 1),
+    (0, (1, 45, 300), 4, 1, 0),
+    (0, (1, 45, 300), 4, 1, 1),    # MRT on the packed-pair segment kernels
+    (0, (1, 70, 520), 8, 1, 0),    # radius-2 stencil: every segment variant, ragged tiles and chunks
+    (0, (1, 70, 520), 8, 1, 1),
+    (0, (1, 37, 260), 10, 1, 0),   # radius 3, the widest halo the segment staging takes
+    (0, (1, 37, 260), 10, 1, 1),
+    (0, (1, 33, 70), 10, 0, 0),
+    (3, (1, 37, 150), 0, 1, 0),
 ])
-def test_every_schedule_variant_matches_oracle(lbm, lattice, shape, stencil, precision):
+def test_every_schedule_variant_matches_oracle(lbm, lattice, shape, stencil, precision, coll):
     """Pin each schedule the autotuner could pick and compare with the oracle
     (FP64: 1e-12; FP32: against the two-pass FP32 result to 1e-6)."""
     nz, ny, nx = shape
-    probe = lbm.Domain(nx, ny, nz, lattice=lattice, stencil=stencil, precision=precision)
+    probe = lbm.Domain(nx, ny, nz, lattice=lattice, stencil=stencil, precision=precision, collision=coll)
     names = [k for k in probe.schedule_report() if k != "chosen"]
     probe.close()
-    ref = oracle.Sim(LAT[lattice], nx, ny, nz, stencil=stencil, G=-5.0, tau=0.9)
+    ref = oracle.Sim(LAT[lattice], nx, ny, nz, stencil=stencil, G=-5.0, tau=0.9, coll=coll)
     ref.init_droplet(1.9, 0.15, min(nx, ny) / 4, 2.0)
     ref.step(23)
     f_ref = ref.get_f()
     results = {}
     for name in names:
-        dom = lbm.Domain(nx, ny, nz, lattice=lattice, stencil=stencil, precision=precision, tau=0.9)
+        dom = lbm.Domain(nx, ny, nz, lattice=lattice, stencil=stencil, precision=precision, tau=0.9,
+                         collision=coll)
         dom.set_schedule(name)
         dom.init_droplet(1.9, 0.15, min(nx, ny) / 4, 2.0)
         dom.step(23)
