@@ -323,10 +323,15 @@ def run_ours(args, world, rank, local):
     Q = lbm.Q_OF[wl["lattice"]]
     per_cell = {"k_fused": (2 * Q + 1) * s, "k_psi": (Q + 1) * s, "k_onepass": 2 * Q * s}
     dom_k = max(kernel_ms, key=kernel_ms.get)
-    bytes_launch = per_cell[dom_k] * cells
-    achieved = bytes_launch / (kernel_ms[dom_k] * 1e-3) / 1e9
-    traffic = recorded_traffic(dom_k, args.workload)
     b_alg = dom.bytes_per_update()
+    # the dominant kernel against the step's algorithmic bytes per update,
+    # B_alg = 2 Q s + 2 s (one read and write of every population, one write
+    # and read of psi); when one kernel is the whole step (the one-pass
+    # schedules) this is the step's roofline, met without the psi traffic
+    alg_cell = b_alg if len(kernel_ms) == 1 else per_cell[dom_k]
+    achieved = alg_cell * cells / (kernel_ms[dom_k] * 1e-3) / 1e9
+    achieved_own = per_cell[dom_k] * cells / (kernel_ms[dom_k] * 1e-3) / 1e9
+    traffic = recorded_traffic(dom_k, args.workload)
     step_gbs = value / world * 1e6 * b_alg / 1e9
 
     # end to end through the public API with host buffers: upload the initial
@@ -360,7 +365,9 @@ def run_ours(args, world, rank, local):
                    "schedule": schedule},
         "roofline": {"bound": "hbm", "kernel": dom_k, "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "algorithmic_bytes_per_cell": per_cell[dom_k], "peak_source": peak_src,
+                     "algorithmic_bytes_per_cell": alg_cell, "peak_source": peak_src,
+                     "kernel_own_bytes_per_cell": per_cell[dom_k],
+                     "frac_of_kernel_own_bytes": round(achieved_own / peak, 4),
                      "kernel_ms": {k: round(v, 5) for k, v in kernel_ms.items()}},
         "step_roofline": {"bytes_per_update": b_alg, "achieved_gbs": round(step_gbs, 1),
                           "frac": round(step_gbs / peak, 4),
@@ -398,13 +405,14 @@ def run_ours(args, world, rank, local):
 
 def sweep_compare(args, n_domains, with_warm, train_domains, epochs, details):
     """Batched FP32 sweep (one persistent-kernel CUDA graph for all domains) against
-    plain FP64 one-domain-per-launch runs of the same domains, both to steady state.
-    With with_warm the batched sweep also runs from the learned warm start, the
-    network trained beforehand on the steady states of a separate draw of
-    domains (another seed), so the timed domains are unseen.  Returns the
-    result line (a dict)."""
+    plain FP64 one-domain-per-launch runs of the same domains, both to steady state
+    (paper_1906_11027_gb300.sweep).  With with_warm the batched sweep also runs
+    from the learned warm start, the network trained beforehand on the steady
+    states of a separate draw of domains (another seed), so the timed domains are
+    unseen.  Every domain's steady max|u| is classified by the sweep's agreement
+    rule.  Returns the result line (a dict)."""
     import torch
-    from paper_1906_11027_gb300 import inputs, lbm, warmstart
+    from paper_1906_11027_gb300 import inputs, lbm, sweep, warmstart
 
     lbm.load()
     doms = inputs.sweep_domains(n_domains)
@@ -414,13 +422,12 @@ def sweep_compare(args, n_domains, with_warm, train_domains, epochs, details):
     w = lbm.Batch(doms[:2], precision=lbm.LBM_FP32_SHIFTED)
     w.step(4)
     w.close()
-    K = 100
     net, train_info = None, None
     if with_warm:
         t0 = time.perf_counter()
         tdoms = inputs.sweep_domains(train_domains, seed=inputs.SWEEP_SEED + 1)
         tb = lbm.Batch(tdoms, precision=lbm.LBM_FP32_SHIFTED)
-        _, tobs, _ = tb.run_to_steady(1e-10, args.sweep_max_steps, K)
+        _, tobs, _ = tb.run_to_steady(sweep.TOL, args.sweep_max_steps, sweep.K)
         Xt, yt, Xv, yv, _ = warmstart.dataset_from_batch(tb, tdoms, tobs)
         tb.close()
         t_gen = time.perf_counter() - t0
@@ -432,107 +439,58 @@ def sweep_compare(args, n_domains, with_warm, train_domains, epochs, details):
                       "train_s": round(time.perf_counter() - t0, 2), "train_loss": loss,
                       "val_mse": float(np.mean((net.predict(Xv) - yv) ** 2)) if len(yv) else None}
 
-    def batched_arm(warm):
-        t0 = time.perf_counter()
-        b = lbm.Batch(doms, precision=lbm.LBM_FP32_SHIFTED)
-        fallbacks = warmstart.batch_warm_init(b, doms, net) if warm else None
-        t_init = time.perf_counter() - t0
-        steps32, obs32, ok32 = b.run_to_steady(1e-10, args.sweep_max_steps, K)
-        torch.cuda.synchronize()
-        t_fp32 = time.perf_counter() - t0
-        # precision policy: a steady current below FP32's velocity resolution is
-        # re-converged in FP64, continued from the FP32 state
-        tiny = [i for i, o in enumerate(obs32) if np.isfinite(o["max_u"]) and o["max_u"] < args.fp64_below]
-        if tiny:
-            b64 = lbm.Batch([doms[i] for i in tiny], precision=lbm.LBM_FP64)
-            for j, i in enumerate(tiny):
-                b64.set_f(j, b.get_f(i))
-            s64, o64, _ = b64.run_to_steady(1e-10, args.sweep_max_steps, K)
-            for j, i in enumerate(tiny):
-                steps32[i] += s64[j]
-                obs32[i] = o64[j]
-            b64.close()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        sched = b.schedule_report()
-        b.close()
-        return dict(t=dt, t_init=t_init, t_fp32=t_fp32, steps=steps32, obs=obs32, ok=ok32, tiny=len(tiny),
-                    fallbacks=fallbacks, schedule=sched)
-
-    plain = batched_arm(False)
-    warm = batched_arm(True) if with_warm else None
+    plain = sweep.batched(doms, None, args.sweep_max_steps, args.fp64_below)
+    warm = sweep.batched(doms, net, args.sweep_max_steps, args.fp64_below) if with_warm else None
+    ref = sweep.one_per_launch(doms, args.sweep_max_steps, sweep.misses_5pct(*[a for a in (plain, warm) if a]))
+    cls_t = sweep.classify(doms, plain, ref, args.fp64_below)
+    cls_w = sweep.classify(doms, warm, ref, args.fp64_below, tanh_arm=plain) if warm else None
+    for arm in (plain, warm):
+        if arm:
+            arm["batch"].close()
     main_arm = warm if warm else plain
-    t_batch, steps32, obs32, ok32 = main_arm["t"], main_arm["steps"], main_arm["obs"], main_arm["ok"]
-    tiny = [None] * main_arm["tiny"]
-    t0 = time.perf_counter()
-    steps64, obs64 = [], []
-    for d in doms:
-        dom = lbm.Domain(d["nx"], d["ny"], G=d["G"], tau=d["tau"], stencil=d["stencil"], precision=lbm.LBM_FP64)
-        dom.init_droplet(d["rho_l"], d["rho_g"], d["R"], d["width"])
-        try:
-            s, ok = dom.run_to_steady(1e-10, args.sweep_max_steps, K)
-            o = dom.observables()
-        except lbm.LbmError as e:  # the BGK model diverges for some (G, tau) pairs
-            if e.code != lbm.LBM_ENONFINITE:
-                raise
-            s, o = args.sweep_max_steps, {"max_u": float("inf")}
-        steps64.append(s)
-        obs64.append(o)
-        dom.close()
-    torch.cuda.synchronize()
-    t_fp64 = time.perf_counter() - t0
+    cls = cls_w if warm else cls_t
+    obs32, obs64, steps32, steps64 = main_arm["obs"], ref["obs"], main_arm["steps"], ref["steps"]
     finite = [i for i in range(len(doms)) if np.isfinite(obs64[i]["max_u"]) and np.isfinite(obs32[i]["max_u"])]
-    diverged = {"fp64": sum(1 for o in obs64 if not np.isfinite(o["max_u"])),
-                "batched_fp32": sum(1 for o in obs32 if not np.isfinite(o["max_u"]))}
     ratio = [abs(obs32[i]["max_u"] / obs64[i]["max_u"] - 1.0) for i in finite] or [float("nan")]
-    # max|u| below FP32 velocity resolution in both arms (dissolved droplet or a
-    # current too small to resolve): relative differences there are not physics
-    small = [i for i in finite if max(obs32[i]["max_u"], obs64[i]["max_u"]) < args.fp64_below]
-    # a droplet in one arm and a dissolved one (max|u| below FP32 resolution) in
-    # the other: near the critical coupling the steady state depends on the start
-    basin = [i for i in finite if i not in small and min(obs32[i]["max_u"], obs64[i]["max_u"]) < args.fp64_below]
-    # precision alone: the tanh-started FP32 batch against the same FP64 runs
-    fin_t = [i for i in range(len(doms)) if np.isfinite(obs64[i]["max_u"]) and np.isfinite(plain["obs"][i]["max_u"])]
-    ratio_t = [abs(plain["obs"][i]["max_u"] / obs64[i]["max_u"] - 1.0) for i in fin_t]
-    small_t = [i for i in fin_t if max(plain["obs"][i]["max_u"], obs64[i]["max_u"]) < args.fp64_below]
     arms = {"batched_fp32_tanh_s": round(plain["t"], 3),
             "tanh_fp32_phase_s": round(plain["t_fp32"], 3),
-            "diverged_tanh_fp32": sum(1 for o in plain["obs"] if not np.isfinite(o["max_u"]))}
+            "diverged_tanh_fp32": sum(1 for o in plain["obs"] if not np.isfinite(o["max_u"])),
+            "steps_total_tanh": int(sum(plain["steps"]))}
     if warm:
+        both = [i for i in range(len(doms)) if np.isfinite(plain["obs"][i]["max_u"])
+                and np.isfinite(warm["obs"][i]["max_u"]) and plain["steps"][i] < args.sweep_max_steps
+                and warm["steps"][i] < args.sweep_max_steps]
         arms.update({"batched_fp32_warm_s": round(warm["t"], 3), "warm_init_s": round(warm["t_init"], 3),
                      "warm_fp32_phase_s": round(warm["t_fp32"], 3),
-                     "warm_fallbacks": warm["fallbacks"],
-                     "steps_total_tanh": int(sum(plain["steps"])), "steps_total_warm": int(sum(warm["steps"]))})
+                     "warm_fallbacks": warm["fallbacks"], "steps_total_warm": int(sum(warm["steps"])),
+                     "converged_in_both": len(both),
+                     "steps_converged_in_both": {"tanh": int(sum(plain["steps"][i] for i in both)),
+                                                 "warm": int(sum(warm["steps"][i] for i in both))}})
     line = {
-        "metric": "sweep_time_to_steady_s", "value": round(t_batch, 3), "unit": "s", "higher_is_better": False,
+        "metric": "sweep_time_to_steady_s", "value": round(main_arm["t"], 3), "unit": "s", "higher_is_better": False,
         "n_gpus": 1, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "d2q9_sweep_warm" if warm else "d2q9_sweep", "domains": len(doms), "cells": cells,
                    "seed": inputs.SWEEP_SEED, "batch_tile": main_arm["schedule"],
                    "rule": "|max|u|(t) - max|u|(t-100)| / 100 < 1e-10 (FP32 adds the floor 1e-6 max|u|/100), "
                            "checked every 100 steps in both arms",
-                   "fp64_below": args.fp64_below, "promoted_to_fp64": len(tiny),
+                   "fp64_below": args.fp64_below, "promoted_to_fp64": main_arm["tiny"],
                    "max_steps": args.sweep_max_steps},
-        "baseline_fp64_one_domain_per_launch_s": round(t_fp64, 3),
-        "speedup": round(t_fp64 / t_batch, 2),
-        "converged": {"batched_fp32": bool(ok32), "fp64": sum(1 for s in steps64 if s < args.sweep_max_steps)},
+        "baseline_fp64_one_domain_per_launch_s": round(ref["t"], 3),
+        "speedup": round(ref["t"] / main_arm["t"], 2),
+        "converged": {"batched_fp32": bool(main_arm["ok"]),
+                      "fp64": sum(1 for s in steps64 if s < args.sweep_max_steps)},
         "steps": {"batched_fp32_total": int(sum(steps32)), "fp64_total": int(sum(steps64))},
-        "diverged": diverged,
+        "diverged": {"fp64": sum(1 for o in obs64 if not np.isfinite(o["max_u"])),
+                     "batched_fp32": sum(1 for o in obs32 if not np.isfinite(o["max_u"]))},
         "per_domain_columns": ["L", "G", "tau", "order", "R", "steps_batched", "steps_fp64", "max_u_batched",
-                               "max_u_fp64", "steps_tanh_fp32", "max_u_tanh_fp32"],
+                               "max_u_fp64", "steps_tanh_fp32", "max_u_tanh_fp32", "class", "class_tanh"],
         "per_domain": [[d["nx"], round(d["G"], 3), d["tau"], d["stencil"], round(d["R"], 1), int(steps32[i]),
                         int(steps64[i]), float("%.4g" % obs32[i]["max_u"]), float("%.4g" % obs64[i]["max_u"]),
-                        int(plain["steps"][i]), float("%.4g" % plain["obs"][i]["max_u"])]
+                        int(plain["steps"][i]), float("%.4g" % plain["obs"][i]["max_u"]), cls[i], cls_t[i]]
                        for i, d in enumerate(doms)] if details else None,
         "max_u_rel_diff": {"max": round(max(ratio), 4), "median": round(float(np.median(ratio)), 4),
-                           "within_5pct": sum(1 for r in ratio if r <= 0.05), "compared": len(finite),
-                           "both_below_fp64_threshold": len(small),
-                           "within_5pct_or_both_below": sum(1 for i, r in zip(finite, ratio)
-                                                            if r <= 0.05 or i in small),
-                           "droplet_in_one_arm_only": len(basin)},
-        "max_u_rel_diff_tanh_fp32_vs_fp64": {
-            "compared": len(fin_t), "within_5pct": sum(1 for r in ratio_t if r <= 0.05),
-            "within_5pct_or_both_below": sum(1 for i, r in zip(fin_t, ratio_t) if r <= 0.05 or i in small_t),
-            "median": round(float(np.median(ratio_t)), 4) if ratio_t else None},
+                           "compared": len(finite), "classes": sweep.counts(cls)},
+        "max_u_rel_diff_tanh_fp32_vs_fp64": {"classes": sweep.counts(cls_t)},
         "arms": arms,
         "warm_start_training": train_info,
     }
@@ -564,8 +522,9 @@ def sweep_summary(args):
         "speedup_warm": ln["speedup"],
         "steps_total": {"tanh_fp32": a["steps_total_tanh"], "warm_fp32": a["steps_total_warm"],
                         "fp64": ln["steps"]["fp64_total"]},
-        "max_u_within_5pct_warm_vs_fp64": ln["max_u_rel_diff"],
-        "max_u_within_5pct_tanh_vs_fp64": ln["max_u_rel_diff_tanh_fp32_vs_fp64"],
+        "steps_converged_in_both": a["steps_converged_in_both"],
+        "agreement_classes_warm_vs_fp64": ln["max_u_rel_diff"]["classes"],
+        "agreement_classes_tanh_vs_fp64": ln["max_u_rel_diff_tanh_fp32_vs_fp64"]["classes"],
         "warm_start_training": ln["warm_start_training"],
         "rule": ln["config"]["rule"],
         "wall_s": round(time.perf_counter() - t0, 1),

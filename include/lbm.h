@@ -290,7 +290,9 @@ int lbm_batch_set_schedule(lbm_batch* b, const char* name);
  * the result).  Weights are FP32 masters with BF16 copies; the GEMMs of training
  * and inference run on the tensor cores with FP32 accumulation.
  * Features (lbm_mlp_features): ((G + 4.9)/0.6, (tau - 0.8)/0.2, (order - 7)/3,
- * (R - 40)/30, d/12).  Parameter vector: W1 [5][128], b1, W2 [128][128], b2, W3,
+ * (min(10/R, 2) - 0.5)/0.4, d/24): the radius enters as a curvature (capped at
+ * that of R = 5), and d spans |d| <= 24, the interface and the bulk on both
+ * sides.  Parameter vector: W1 [5][128], b1, W2 [128][128], b2, W3,
  * b3, W4, b4, W5 [128][1], b5 (50,433 floats); z = h W + b. */
 typedef struct lbm_mlp lbm_mlp;
 int lbm_mlp_create(lbm_mlp** out, uint64_t seed);   /* He-uniform weights from SplitMix64(seed) */
@@ -316,7 +318,10 @@ int lbm_mlp_load(lbm_mlp** out, const char* path);
  * the network's profile for the context's G, tau and stencil order at radius
  * R_eff, R_eff chosen by bisection so that the total mass equals that of the
  * tanh droplet (rho_l, rho_g, R, width) of lbm_init_droplet, the remainder removed
- * by a uniform shift; populations f = w_b rho0.  Falls back to the tanh droplet
+ * by a uniform shift; populations f = w_b rho0.  On D3Q19 the network, which
+ * holds 2-D profiles, is evaluated at radius R_eff/2, the 2-D droplet with the
+ * same Laplace pressure jump (2 sigma/R in 3-D), and the profile is placed at
+ * R_eff.  Falls back to the tanh droplet
  * (*used_fallback = 1) if the network gives a non-finite or non-positive
  * density, and for G > -4.5, where close to the critical coupling G_c = -4 the
  * steady state (droplet or none) depends on the initial state.  *R_eff_out (may
@@ -337,7 +342,10 @@ int lbm_init_droplet_learned(lbm_ctx* ctx, lbm_mlp* net, double R, double rho_l,
  *             ignored for LBM_FP64; for a context's buffer it is the value
  *             lbm_reference_density returns)
  *   stream    cudaStream_t the kernels run on (NULL: the legacy default stream);
- *             the call synchronises it
+ *             the call synchronises it.  The caller orders it after the work
+ *             that writes f_dev: a context steps on its own stream, which is a
+ *             non-blocking stream when lbm_params.stream was NULL, so pass that
+ *             stream or synchronise it first
  *   out_host  4 doubles: sum over every cell of rho, then of sum_b f_b c_b
  *             (x, y, z), the momentum before the half-force term.  With a wall
  *             the sums include the solid band (lbm_observables takes its

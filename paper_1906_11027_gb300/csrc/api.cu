@@ -644,7 +644,7 @@ int lbm_init_droplet_learned(lbm_ctx* c, lbm_mlp* net, double R, double rho_l, d
     }
     Scratch rho0(c, sizeof(double) * c->N);
     constexpr int T = 1024;
-    constexpr double kDmax = 12.0;
+    constexpr double kDmax = kMlpDmax;
     Scratch table(c, sizeof(float) * T);
     if (!rho0.p || !table.p) return fail(LBM_ENOMEM, "scratch allocation failed");
     // target mass of the tanh start
@@ -656,8 +656,12 @@ int lbm_init_droplet_learned(lbm_ctx* c, lbm_mlp* net, double R, double rho_l, d
     double m0 = 0.0;
     if (int rc = field_mean(c, rho0.d(), &m0)) return rc;
     const int dim = c->li.D;
+    // The network holds 2-D profiles, whose Laplace jump is sigma/R; a 3-D
+    // droplet's is 2 sigma/R, the jump of a 2-D droplet of radius R/2, so a 3-D
+    // droplet's profile is taken at that radius (and placed at R).
+    const double r_in = (dim == 3) ? 0.5 : 1.0;
     auto mass_at = [&](double Re, double* mean) -> int {
-        if (int rc = mlp_profile_table(net, c->prm.G, c->prm.tau, (double)c->order, Re, T, kDmax,
+        if (int rc = mlp_profile_table(net, c->prm.G, c->prm.tau, (double)c->order, r_in * Re, T, kDmax,
                                        static_cast<float*>(table.p)))
             return rc;
         LBM_CK(launch_field_from_table(c->dp, dim, static_cast<const float*>(table.p), T, kDmax, Re, rho0.d(),

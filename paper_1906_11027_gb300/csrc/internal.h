@@ -121,6 +121,8 @@ cudaError_t launch_wait_probe(unsigned* err, cudaStream_t s);
 
 // Warm-start network (mlp.cu): evaluates the network's density at T signed
 // distances evenly spaced over [-dmax, dmax] for (G, tau, order, R) into table_dev.
+// The network's distance input spans |d| <= kMlpDmax.
+constexpr double kMlpDmax = 24.0;
 }  // namespace lbm
 struct lbm_mlp;
 namespace lbm {

@@ -235,13 +235,20 @@ inline unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1)
 }  // namespace
 
 // Feature scaling of the warm-start network (shared by training data and inference).
+// The radius enters as the curvature 10/R: the steady profile depends on R
+// through the Laplace pressure sigma/R, and a droplet larger than any trained
+// one then lies next to the trained range (curvature near 0) instead of far
+// outside it.  The curvature is capped at that of R = 5, below the smallest
+// trained droplets, so that the small radii the mass bisection tries stay in
+// range.  d spans the interface and the bulk plateaus on both sides.
 __host__ __device__ inline void mlp_features(double G, double tau, double order, double R, double d, float* x)
 {
+    const double kappa = R > 5.0 ? 10.0 / R : 2.0;
     x[0] = (float)((G + 4.9) / 0.6);
     x[1] = (float)((tau - 0.8) / 0.2);
     x[2] = (float)((order - 7.0) / 3.0);
-    x[3] = (float)((R - 40.0) / 30.0);
-    x[4] = (float)(d / 12.0);
+    x[3] = (float)((kappa - 0.5) / 0.4);
+    x[4] = (float)(d / kMlpDmax);
 }
 
 }  // namespace lbm

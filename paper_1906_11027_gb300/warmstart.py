@@ -1,7 +1,8 @@
 """Training data and training of the warm-start network.
 
 Steady droplets from the batched sweep become samples (G, tau, order, R_s, d) -> rho
-for every cell within |d| <= 12 of the interface, where R_s is the steady
+for every cell within |d| <= 24 of the interface (the interface and the bulk
+plateaus on both sides, whose densities set the mass balance of a start), where R_s is the steady
 droplet's equimolar radius (the radius of a sharp droplet of the same excess
 mass, R_s^2 pi = sum (rho - rho_g) / (rho_l - rho_g)) and d = r - R_s.  The same
 radius is what lbm_init_droplet_learned bisects on, so training and inference
@@ -14,7 +15,7 @@ import numpy as np
 
 from . import lbm
 
-DMAX = 12.0
+DMAX = 24.0
 MAX_G = -4.5        # the library keeps the tanh start above this coupling
 MIN_CONTRAST = 0.2  # rho_l - rho_g of a steady droplet (a dissolved one is not a sample)
 

@@ -190,3 +190,34 @@ def test_learned_warm_start_reaches_the_plain_steady_state(lbm):
     assert np.abs(res["warm"][3] - res["plain"][3]).max() <= 1e-6
     assert res["warm"][2] == pytest.approx(res["plain"][2], rel=0.05)
     assert res["warm"][0] < res["plain"][0]
+
+
+def test_learned_start_saves_steps_on_a_large_droplet(lbm):
+    """A 512^2 droplet (R = 100, G = -5, tau = 1, 4th-order stencil), larger than
+    any droplet of the training draw (128 domains of the sweep, seed 11028, sides
+    up to 256).  The network's radius input is a curvature, so this droplet lies
+    next to the trained range: the learned start puts the bulk densities and the
+    radius near their steady values and reaches the plain run's steady state
+    (max |drho| <= 1e-6, max|u| within 5%, FP64 rule at 1e-13) in fewer steps."""
+    from paper_1906_11027_gb300 import inputs, warmstart
+    tdoms = inputs.sweep_domains(128, seed=inputs.SWEEP_SEED + 1)
+    tb = lbm.Batch(tdoms, precision=lbm.LBM_FP32_SHIFTED)
+    _, tobs, _ = tb.run_to_steady(1e-10, 200000, 100)
+    Xt, yt, _, _, _ = warmstart.dataset_from_batch(tb, tdoms, tobs)
+    tb.close()
+    net, _ = warmstart.train(Xt, yt, epochs=60)
+    res = {}
+    for mode in ("plain", "warm"):
+        dom = lbm.Domain(512, 512, G=-5.0, tau=1.0, stencil=4)
+        if mode == "plain":
+            dom.init_droplet(2.0, 0.15, 100.0, 2.0)
+        else:
+            fb, _ = dom.init_droplet_learned(net, 100.0, 2.0, 0.15, 2.0)
+            assert not fb
+        steps, ok = dom.run_to_steady(1e-13, 400000, 100)
+        assert ok
+        res[mode] = (steps, dom.observables()["max_u"], dom.fields()["rho"])
+        dom.close()
+    assert np.abs(res["warm"][2] - res["plain"][2]).max() <= 1e-6
+    assert res["warm"][1] == pytest.approx(res["plain"][1], rel=0.05)
+    assert res["warm"][0] < res["plain"][0], (res["plain"][0], res["warm"][0])

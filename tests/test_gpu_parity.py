@@ -334,7 +334,8 @@ def test_one_pass_matches_two_pass(lbm, lattice, shape, stencil, coll, precision
         d.init_droplet(1.9, 0.15, min(nx, ny) / 4, 2.0)
         d.step(57)
     a, b = doms[0].get_f(), doms[1].get_f()
-    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+    # FP32: the packed-pair kernels order their float operations differently
+    assert np.abs(a - b).max() <= (1e-13 if precision == 0 else 1e-5) * np.abs(a).max()
 
 
 def test_one_pass_ragged_3d_against_oracle(lbm):
@@ -354,8 +355,8 @@ def test_one_pass_ragged_3d_against_oracle(lbm):
     (1, (9, 10, 256), 4, 1, 0),
     (1, (9, 10, 256), 4, 1, 1),    # MRT on the packed-pair whole-row kernels
     (1, (9, 10, 200), 4, 1, 0),    # runtime row lengths: 200 (three rows per item), ragged rows
-    (1, (7, 11, 300), 4, 1, 1),    # 300 (two rows per item), MRT
-    (1, (6, 5, 420), 4, 1, 0),     # 420 (one row per item)
+    (1, (8, 11, 300), 4, 1, 1),    # 300 (two rows per item), MRT
+    (1, (8, 9, 420), 4, 1, 0),     # 420 (one row per item)
     (1, (21, 19, 37), 6, 1, 0),
     (1, (20, 16, 33), 4, 0, 0),
     (1, (13, 11, 256), 4, 0, 1),
