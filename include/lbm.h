@@ -323,8 +323,9 @@ int lbm_mlp_load(lbm_mlp** out, const char* path);
  * same Laplace pressure jump (2 sigma/R in 3-D), and the profile is placed at
  * R_eff.  Falls back to the tanh droplet
  * (*used_fallback = 1) if the network gives a non-finite or non-positive
- * density, and for G > -4.5, where close to the critical coupling G_c = -4 the
- * steady state (droplet or none) depends on the initial state.  *R_eff_out (may
+ * density, and for G > -4.65, where close to the critical coupling G_c = -4 the
+ * steady state (droplet or none, and the current it carries) depends on the
+ * initial state.  *R_eff_out (may
  * be NULL) = the radius used. */
 int lbm_init_droplet_learned(lbm_ctx* ctx, lbm_mlp* net, double R, double rho_l, double rho_g, double width,
                              int* used_fallback, double* R_eff_out);

@@ -13,6 +13,7 @@
 
 #include "../../include/lbm.h"
 #include "internal.h"
+#include "trace.h"
 
 using namespace lbm;
 
@@ -106,9 +107,10 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn()
 
 constexpr int kGraphSteps = 16;   // steps per captured graph (even)
 // Couplings weaker than this use the tanh start in lbm_init_droplet_learned:
-// within ~0.5 of G_c = -4 a droplet may dissolve or persist depending on the
-// initial state, so a learned start need not reach the plain run's steady state.
-constexpr double kWarmStartMaxG = -4.5;
+// within ~0.65 of G_c = -4 a droplet may dissolve, persist or settle with
+// another current depending on the initial state, so a learned start need not
+// reach the plain run's steady state.
+constexpr double kWarmStartMaxG = -4.65;
 constexpr int kNBlocksMax = 152 * 16;
 constexpr uint32_t kMagic = 0x4c424d31u;  // "LBM1"
 
@@ -774,6 +776,7 @@ int lbm_set_populations(lbm_ctx* c, const double* f_host)
 
 int lbm_step(lbm_ctx* c, int64_t n)
 {
+    lbm::TraceRange trace("lbm_step");
     if (!c || n < 0) return fail(LBM_EINVAL, "bad argument");
     if (int rc = set_device(c)) return rc;
     if (n > 0)
@@ -876,6 +879,7 @@ int lbm_set_schedule(lbm_ctx* c, const char* name)
 
 int lbm_observables(lbm_ctx* c, lbm_obs* out)
 {
+    lbm::TraceRange trace("lbm_observables");
     if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
     if (int rc = set_device(c)) return rc;
     LaunchArgs a = c->args();
@@ -932,6 +936,7 @@ int lbm_diag_wait_timeout(lbm_ctx* c)
 
 int lbm_run_to_steady(lbm_ctx* c, double tol, int64_t max_steps, int64_t check_every, int64_t* steps_out)
 {
+    lbm::TraceRange trace("lbm_run_to_steady");
     if (!c || !(tol > 0.0) || max_steps < 0 || check_every < 1) return fail(LBM_EINVAL, "bad argument");
     lbm_obs o;
     if (int rc = lbm_observables(c, &o)) return rc;

@@ -24,6 +24,7 @@
 
 #include "../../include/lbm.h"
 #include "internal.h"
+#include "trace.h"
 #include "kernels.cuh"
 
 namespace lbm {
@@ -1091,6 +1092,7 @@ int lbm_batch_destroy(lbm_batch* b)
 // Advances every active domain by n steps (no steady check).
 int lbm_batch_step(lbm_batch* b, int64_t n)
 {
+    lbm::TraceRange trace("lbm_batch_step");
     if (!b || n < 0) return set_last_error(LBM_EINVAL, "lbm_batch_step: bad argument");
     LBM_BCK(cudaSetDevice(b->device));
     if (n > 0)
@@ -1112,6 +1114,7 @@ int lbm_batch_step(lbm_batch* b, int64_t n)
 int lbm_batch_run_to_steady(lbm_batch* b, double tol, int64_t max_steps, int64_t check_every,
                             int64_t* steps_per_domain, lbm_obs* obs_per_domain)
 {
+    lbm::TraceRange trace("lbm_batch_run_to_steady");
     if (!b || !(tol > 0.0) || max_steps < 0 || check_every < 2 || check_every % 2)
         return set_last_error(LBM_EINVAL, "lbm_batch_run_to_steady: bad argument (check_every must be even)");
     LBM_BCK(cudaSetDevice(b->device));

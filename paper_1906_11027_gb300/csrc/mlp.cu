@@ -19,6 +19,7 @@
 
 #include "../../include/lbm.h"
 #include "internal.h"
+#include "trace.h"
 
 namespace lbm {
 namespace {
@@ -570,6 +571,7 @@ int lbm_mlp_loss_grad(lbm_mlp* n, const float* X, const float* t, int rows, doub
 int lbm_mlp_train(lbm_mlp* n, const float* X, const float* t, int64_t rows, int epochs, double lr, int batch,
                   double* final_loss)
 {
+    lbm::TraceRange trace("lbm_mlp_train");
     if (!n || !X || !t || rows < 1 || epochs < 0 || !(lr > 0.0) || batch < 16)
         return set_last_error(LBM_EINVAL, "bad argument");
     MCK(cudaSetDevice(n->device));

@@ -16,7 +16,7 @@ import numpy as np
 from . import lbm
 
 DMAX = 24.0
-MAX_G = -4.5        # the library keeps the tanh start above this coupling
+MAX_G = -4.65       # the library keeps the tanh start above this coupling
 MIN_CONTRAST = 0.2  # rho_l - rho_g of a steady droplet (a dissolved one is not a sample)
 
 
