@@ -3027,6 +3027,8 @@ constexpr VariantList make_variants()
                 add("onepass_rowp2_256x3_s2", &launch_onepass_rowp2<LAT, ORD, 0, 256, 3, 2>, 1, 256);
                 add("onepass_rowp2_256x3_s2_np", &launch_onepass_rowp2<LAT, ORD, 0, 256, 3, 2, false>, 1, 256);
                 add("onepass_rowp2_w256x3_s2_np", &launch_onepass_rowp2w<LAT, ORD, 0, 256, 3, 2, false>, 4, 0, 256);
+                add("onepass_rowp2_w224x3_s2", &launch_onepass_rowp2w<LAT, ORD, 0, 224, 3, 2, true>, 4, 0, 224);
+                add("onepass_rowp2_w208x2_s3", &launch_onepass_rowp2w<LAT, ORD, 0, 208, 2, 3, true>, 4, 0, 208);
                 add("onepass_rowp2_w344x2_s2", &launch_onepass_rowp2w<LAT, ORD, 0, 344, 2, 2, true>, 4, 0, 344);
                 add("onepass_rowp2_w456x1_s2", &launch_onepass_rowp2w<LAT, ORD, 0, 456, 1, 2, true>, 4, 0, 456);
                 add("onepass_row128x4_z32_s3", &launch_onepass_row<LAT, ORD, COLL, Real, 128, 4, 32, 3, 0>, 1, 128);
@@ -3051,6 +3053,8 @@ constexpr VariantList make_variants()
             add("onepass_rowp2_256x2_s2", &launch_onepass_rowp2<LAT, ORD, 1, 256, 2, 2>, 1, 256);
             add("onepass_rowp2_256x3_s2", &launch_onepass_rowp2<LAT, ORD, 1, 256, 3, 2>, 1, 256);
             add("onepass_rowp2_w256x3_s2_np", &launch_onepass_rowp2w<LAT, ORD, 1, 256, 3, 2, false>, 4, 0, 256);
+            add("onepass_rowp2_w224x3_s2", &launch_onepass_rowp2w<LAT, ORD, 1, 224, 3, 2, true>, 4, 0, 224);
+            add("onepass_rowp2_w208x2_s3", &launch_onepass_rowp2w<LAT, ORD, 1, 208, 2, 3, true>, 4, 0, 208);
             add("onepass_rowp2_w344x2_s2", &launch_onepass_rowp2w<LAT, ORD, 1, 344, 2, 2, true>, 4, 0, 344);
             add("onepass_rowp2_w456x1_s2", &launch_onepass_rowp2w<LAT, ORD, 1, 456, 1, 2, true>, 4, 0, 456);
         }

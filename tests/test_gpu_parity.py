@@ -356,6 +356,7 @@ def test_one_pass_ragged_3d_against_oracle(lbm):
     (1, (9, 10, 256), 4, 1, 1),    # MRT on the packed-pair whole-row kernels
     (1, (9, 10, 200), 4, 1, 0),    # runtime row lengths: 200 (three rows per item), ragged rows
     (1, (8, 11, 300), 4, 1, 1),    # 300 (two rows per item), MRT
+    (1, (8, 9, 136), 4, 1, 1),     # 136: every run-time width, MRT
     (1, (8, 9, 420), 4, 1, 0),     # 420 (one row per item)
     (1, (21, 19, 37), 6, 1, 0),
     (1, (20, 16, 33), 4, 0, 0),
