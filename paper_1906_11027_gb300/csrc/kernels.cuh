@@ -1991,6 +1991,231 @@ __global__ void __launch_bounds__((NXMAX / 2 * TY + 31) / 32 * 32 + (PRODW ? 32 
     if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
 }
 
+// Whole-row packed-pair schedule for stencils of radius R >= 2 (D3Q19 with the
+// 6th-order stencil): the staging, item walk and packed collision of
+// k_onepass_rowp2, with the row length read at run time (nx <= NXMAX, a
+// multiple of 4).  At radius 2 a slab's stage holds TY + 4 rows per direction,
+// so a 256-cell row allows only few stages; with NSTG = 1 the copy of slab
+// m + R + 1 starts right after every thread has formed psi of slab m + R and
+// overlaps the force and collision of slab m.  Because fewer than 2R stages
+// may exist, the 2R warm-up slabs of an item are consumed one at a time, each
+// followed by a barrier after which the issuing warp refills the stage.  The
+// interior populations wait R slabs in a register delay line (d0 collides
+// next, d1 one slab later).  The psi ring keeps R wrapped columns on each side.
+template <int LAT, int ORD, int COLL, int TY, int NSTG, bool PRODW, int NXMAX>
+__global__ void __launch_bounds__((NXMAX / 2 * TY + 31) / 32 * 32 + (PRODW ? 32 : 0), 1)
+    k_onepass_rowr(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, int zc, int nitems)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<3, ORD>;
+    constexpr int R = S::radius;
+    constexpr int Q = L::Q;
+    static_assert(L::D == 3 && R == 2 && L::reach == 1, "radius-2 row staging for 3-D reach-1 lattices");
+    constexpr int EY = TY + 2 * R;
+    constexpr int NS = 2 * R + 2;
+    static_assert((NXMAX / 2 * TY + 31) / 32 * 32 + 32 <= 1024 && NXMAX % 4 == 0, "block shape");
+    static_assert(NSTG >= 1 && NSTG <= 32, "stages");
+    const int nx = p.nx;
+    const int half = nx / 2;
+    const int NT = (half * TY + 31) / 32 * 32;  // compute threads, whole warps
+    const int EX = nx + 2 * R;
+    const int E = EX * EY;
+    const int STG = Q * EY * nx;
+    __shared__ alignas(8) unsigned long long bars[NSTG];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    float* stage = reinterpret_cast<float*>(dyn_smem);  // [NSTG][STG]
+    float* ring = stage + NSTG * STG;                    // [NS][E]
+
+    const int nty = (p.ny + TY - 1) / TY;
+    const int nm = p.nz;
+    const int plane = nx * p.ny;
+    const int tid = threadIdx.x;
+    const int tp = tid % half, ty = tid / half;  // pair index along x, row in the tile (ty >= TY: idle lane)
+    const int x0 = 2 * tp;
+    const int lane = tid & 31;
+    const bool producer = PRODW && tid >= NT;
+    const bool issuer = PRODW ? producer : (tid / 32 == NT / 32 - 1);
+
+    if (tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    int cby = 0, cbz = 0;
+    const float* src_b = nullptr;
+    sfor<Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int vy = L::T.v[b][1], vz = L::T.v[b][2];
+        if (lane == b) {
+            cby = vy;
+            cbz = vz;
+            src_b = P.in[b];
+        }
+    });
+    // the copy sequence: for every item of this block, slabs m0 - R .. m1 - 1 + R
+    int p_it = blockIdx.x, p_y0 = 0, p_next = 0, p_last = -1;
+    auto p_load_item = [&]() {
+        if (p_it >= nitems) return;
+        const int m0 = (p_it / nty) * zc;
+        const int m1 = (m0 + zc < nm) ? m0 + zc : nm;
+        p_y0 = (p_it % nty) * TY;
+        p_next = m0 - R;
+        p_last = m1 - 1 + R;
+    };
+    p_load_item();
+    long long issued = 0;
+    auto issue_next = [&]() {
+        const int slot = static_cast<int>(issued % NSTG);
+        const uint32_t bar = smem_u32(&bars[slot]);
+        if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(STG * sizeof(float)));
+        __syncwarp();
+        if (lane < Q) {
+            fence_proxy_async_smem();
+            const float* pl = src_b + static_cast<long long>(wrap_any(p_next - cbz, nm)) * plane;
+            uint32_t dst = smem_u32(stage + slot * STG + lane * (EY * nx));
+            int y = p_y0 - R - cby, left = EY;
+            while (left > 0) {
+                const int yw = wrap_any(y, p.ny);
+                const int n = (p.ny - yw < left) ? p.ny - yw : left;
+                bulk_g2s(dst, pl + static_cast<long long>(yw) * nx, static_cast<uint32_t>(n * nx * sizeof(float)), bar);
+                dst += static_cast<uint32_t>(n * nx * sizeof(float));
+                y += n;
+                left -= n;
+            }
+        }
+        __syncwarp();
+        ++issued;
+        if (++p_next > p_last) {
+            p_it += gridDim.x;
+            p_load_item();
+        }
+    };
+    auto issue_upto = [&](long long consumed) {
+        while (p_it < nitems && issued < consumed + NSTG) issue_next();
+    };
+
+    uint32_t phase = 0;
+    bool ok = true;
+    long long consumed = 0;
+    auto wait_seq = [&](long long q) -> const float* {
+        const int slot = static_cast<int>(q % NSTG);
+        if (ok && !mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;  // after a timeout, stop waiting
+        phase ^= 1u << slot;
+        return stage + slot * STG;
+    };
+    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;  // pull column of c_x = +1 for the first cell
+    const int xr = (x0 + 2 == nx) ? 0 : x0 + 2;  // pull column of c_x = -1 for the second cell
+    auto load_pair = [&](const float* st, int fy, float2 (&f)[Q]) {
+        const float* r = st + fy * nx;
+        sfor<Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int vx = L::T.v[b][0];
+            const float* rb = r + b * (EY * nx);
+            if (vx == 0)
+                f[b] = *reinterpret_cast<const float2*>(rb + x0);
+            else if (vx > 0)
+                f[b] = make_float2(rb[xl], rb[x0]);
+            else
+                f[b] = make_float2(rb[x0 + 1], rb[xr]);
+        });
+    };
+    auto rho_psi2 = [&](const float2 (&f)[Q]) {
+        float2 sum = p2(0.f);
+        sfor<Q>([&](auto bI) { sum = add2(sum, f[decltype(bI)::value]); });
+        return make_float2(psi_of<LAT>(p.rho_bar_f + sum.x, p), psi_of<LAT>(p.rho_bar_f + sum.y, p));
+    };
+    // psi of the pair into ring row fy, and into the R wrapped columns on each side
+    auto put_psi2 = [&](float* dst, int fy, float2 v) {
+        float* row = dst + fy * EX;
+        row[x0 + R] = v.x;
+        row[x0 + 1 + R] = v.y;
+        if (x0 < R) {
+            row[x0 + nx + R] = v.x;
+            if (x0 + 1 < R) row[x0 + 1 + nx + R] = v.y;
+        }
+        if (x0 + 1 >= nx - R) {
+            row[x0 + 1 - nx + R] = v.y;
+            if (x0 >= nx - R) row[x0 - nx + R] = v.x;
+        }
+    };
+    float2 fnxt[Q], d0[Q], d1[Q];
+    auto psi_slab = [&](int s, long long q) {
+        const float* st = wait_seq(q);
+        if (ty >= TY) return;  // idle lane: keeps the barrier phases only
+        float* dst = ring + ring_slot(s, NS) * E;
+        load_pair(st, ty + R, fnxt);
+        put_psi2(dst, ty + R, rho_psi2(fnxt));
+        for (int k = ty; k < 2 * R; k += TY) {
+            const int fy = (k < R) ? k : EY - 2 * R + k;
+            float2 f[Q];
+            load_pair(st, fy, f);
+            put_psi2(dst, fy, rho_psi2(f));
+        }
+    };
+    auto shift = [&]() {
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            d0[b] = d1[b];
+            d1[b] = fnxt[b];
+        }
+    };
+
+    if (issuer) issue_upto(0);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int y0 = (it % nty) * TY;
+        const int m0 = (it / nty) * zc;
+        const int m1 = (m0 + zc < nm) ? m0 + zc : nm;
+        // warm-up: psi of slabs m0 - R .. m0 + R - 1, one slab per barrier
+        for (int k = 0; k < 2 * R; ++k) {
+            if (!producer) {
+                psi_slab(m0 - R + k, consumed);
+                shift();
+            }
+            ++consumed;
+            __syncthreads();
+            if (issuer) issue_upto(consumed);
+        }
+        const bool active = !producer && ty < TY && (y0 + ty) < p.ny;
+        const int cell_xy = (y0 + ty) * nx + x0;
+        for (int m = m0; m < m1; ++m) {
+            if (!producer) psi_slab(m + R, consumed);
+            ++consumed;
+            __syncthreads();
+            if (issuer) issue_upto(consumed);
+            if (active) {
+                // force (Eq. 1) of both cells from the psi ring, opposite vectors paired
+                const float* base[2 * R + 1];
+#pragma unroll
+                for (int k = 0; k < 2 * R + 1; ++k) base[k] = ring + ring_slot(m - R + k, NS) * E + (ty + R) * EX + x0 + R;
+                float2 ax = p2(0.f), ay = p2(0.f), az = p2(0.f);
+                sfor<S::n / 2>([&](auto kI) {
+                    constexpr int a = 2 * decltype(kI)::value;
+                    constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1], ez = S::T.v[a][2];
+                    constexpr double wt = S::T.w[a] * L::cs2;
+                    const float* pp = base[ez + R] + ey * EX + ex;
+                    const float* pm = base[R - ez] - ey * EX - ex;
+                    const float2 d = sub2(make_float2(pp[0], pp[1]), make_float2(pm[0], pm[1]));
+                    if (ex != 0) ax = fma2(p2(float(wt * ex)), d, ax);
+                    if (ey != 0) ay = fma2(p2(float(wt * ey)), d, ay);
+                    if (ez != 0) az = fma2(p2(float(wt * ez)), d, az);
+                });
+                const float2 gp = mul2(p2(-p.G_f), make_float2(base[R][0], base[R][1]));
+                const float2 F[3] = {mul2(gp, ax), mul2(gp, ay), mul2(gp, az)};
+                collide2<LAT, COLL>(d0, F, p);
+                const int c = m * plane + cell_xy;
+                sfor<Q>([&](auto bI) {
+                    constexpr int b = decltype(bI)::value;
+                    __stcs(reinterpret_cast<float2*>(P.out[b] + c), d0[b]);
+                });
+            }
+            if (!producer) shift();
+        }
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
+}
+
 // Packed-pair form of the segment schedule k_onepass_seg (FP32 BGK, 2-D reach-1
 // lattices): a compute thread owns the x-adjacent cells (2t, 2t + 1) of the
 // tile, so the directions with c_x = 0 come from the staged segment as one
@@ -2707,8 +2932,8 @@ cudaError_t launch_onepass(const LaunchArgs& a, cudaStream_t s)
 
 // Chunk length of the persistent whole-row schedules (one block per SM): the
 // chunk count that minimises the largest number of slabs a block marches, its
-// items x (chunk + the two warm-up slabs).
-inline int rowp_chunk(int nz, int nty, int nsm)
+// items x (chunk + the warm-up slabs, 2R).
+inline int rowp_chunk(int nz, int nty, int nsm, int warm = 2)
 {
     int zc = nz;
     long long best = -1;
@@ -2716,7 +2941,7 @@ inline int rowp_chunk(int nz, int nty, int nsm)
         const int len = (nz + nc - 1) / nc;
         const int used = (nz + len - 1) / len;
         const long long per_block = (static_cast<long long>(nty) * used + nsm - 1) / nsm;
-        const long long cost = per_block * (len + 2);
+        const long long cost = per_block * (len + warm);
         if (best < 0 || cost < best) {
             best = cost;
             zc = len;
@@ -2767,6 +2992,35 @@ cudaError_t launch_onepass_rowp2w(const LaunchArgs& a, cudaStream_t s)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int zc = rowp_chunk(a.p.nz, nty, nsm);
+    const int nitems = nty * ((a.p.nz + zc - 1) / zc);
+    const int grid = nitems < nsm ? nitems : nsm;
+    const int threads = (nx / 2 * TY + 31) / 32 * 32 + (PRODW ? 32 : 0);
+    const auto P = make_pops<float, Q>(a.fin, a.fout, a.p.N);
+    kern<<<grid, threads, dyn_of(nx), s>>>(P, a.p, zc, nitems);
+    return cudaGetLastError();
+}
+
+// Radius-2 whole-row schedule (k_onepass_rowr), any row length nx <= NXMAX
+// that is a multiple of 4.
+template <int LAT, int ORD, int COLL, int NXMAX, int TY, int NSTG, bool PRODW>
+cudaError_t launch_onepass_rowr(const LaunchArgs& a, cudaStream_t s)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    constexpr int R = Stencil<3, ORD>::radius;
+    constexpr int EY = TY + 2 * R;
+    constexpr int NS = 2 * R + 2;
+    auto dyn_of = [](int nx) {
+        return sizeof(float) * (static_cast<size_t>(NSTG) * Q * EY * nx + static_cast<size_t>(NS) * (nx + 2 * R) * EY);
+    };
+    auto kern = &k_onepass_rowr<LAT, ORD, COLL, TY, NSTG, PRODW, NXMAX>;
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn_of(NXMAX)); e != cudaSuccess) return e;
+    const int nx = a.p.nx;
+    if (nx % 4 != 0 || nx < 8 || nx > NXMAX) return cudaErrorInvalidValue;
+    const int nty = (a.p.ny + TY - 1) / TY;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int zc = rowp_chunk(a.p.nz, nty, nsm, 2 * R);
     const int nitems = nty * ((a.p.nz + zc - 1) / zc);
     const int grid = nitems < nsm ? nitems : nsm;
     const int threads = (nx / 2 * TY + 31) / 32 * 32 + (PRODW ? 32 : 0);
@@ -3042,6 +3296,12 @@ constexpr VariantList make_variants()
                 add("onepass_lai_64x4_z16_b3", &launch_onepass_la<LAT, ORD, COLL, Real, 64, 4, 16, 3, 0>);
                 add("onepass_lai_64x4_z16_b4", &launch_onepass_la<LAT, ORD, COLL, Real, 64, 4, 16, 4, 0>);
                 add("onepass_lai_64x4_z32_b3", &launch_onepass_la<LAT, ORD, COLL, Real, 64, 4, 32, 3, 0>);
+            }
+            if constexpr (Stencil<3, ORD>::radius == 2) {
+                add("onepass_rowr_w256x2_s1", &launch_onepass_rowr<LAT, ORD, COLL, 256, 2, 1, true>, 4, 0, 256);
+                add("onepass_rowr_w256x2_s1_np", &launch_onepass_rowr<LAT, ORD, COLL, 256, 2, 1, false>, 4, 0, 256);
+                add("onepass_rowr_w256x3_s1_np", &launch_onepass_rowr<LAT, ORD, COLL, 256, 3, 1, false>, 4, 0, 256);
+                add("onepass_rowr_w256x1_s2", &launch_onepass_rowr<LAT, ORD, COLL, 256, 1, 2, true>, 4, 0, 256);
             }
             add("onepass_la_32x8_z16_b2", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 2, 1>);
             add("onepass_lai_32x8_z16_b3", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 3, 0>);

@@ -291,23 +291,27 @@ def test_full_size_d3q19_256_fp32_against_oracle(lbm):
     assert dom.observables()["mass"] == pytest.approx(m0, rel=1e-6)
 
 
-@pytest.mark.parametrize("coll", [0, 1])
-def test_full_size_headline_schedule_populations_against_oracle(lbm, coll):
+@pytest.mark.parametrize("coll,stencil,schedule", [(0, 4, "onepass_rowp2_256x3_s2_np"),
+                                                  (1, 4, "onepass_rowp2_256x3_s2_np"),
+                                                  (0, 6, "onepass_rowr_w256x3_s1_np")])
+def test_full_size_headline_schedule_populations_against_oracle(lbm, coll, stencil, schedule):
     """The benchmark's schedule at the benchmark's size, populations compared
     cell by cell: D3Q19, FP32 deviations, 256^3, psi = 1 - exp(-rho), G = -5,
     4th-order stencil, droplet R = 40, with the packed-pair whole-row kernel
-    (three rows per item, no producer warp) pinned, BGK and MRT.  At this size
-    every block walks several items, so the copy sequence runs on across item
-    boundaries.  After three steps every population lies within 2e-6 of the
-    largest (FP32 storage of deviations of size ~0.3, rounded at 2^-24)."""
+    (three rows per item, no producer warp) pinned, BGK and MRT; and the
+    6th-order stencil on the radius-2 whole-row kernel (one stage).  At this
+    size every block walks several items, so the copy sequence runs on across
+    item boundaries.  After three steps every population lies within 2e-6 of
+    the largest (FP32 storage of deviations of size ~0.3, rounded at 2^-24)."""
     n = 256
-    dom = lbm.Domain(n, n, n, lattice=lbm.LBM_D3Q19, stencil=4, precision=1, G=-5.0, tau=1.0, collision=coll)
-    dom.set_schedule("onepass_rowp2_256x3_s2_np")
+    dom = lbm.Domain(n, n, n, lattice=lbm.LBM_D3Q19, stencil=stencil, precision=1, G=-5.0, tau=1.0,
+                     collision=coll)
+    dom.set_schedule(schedule)
     dom.init_droplet(2.0, 0.15, 40.0, 2.0)
     dom.step(3)
     f_gpu = dom.get_f()
     dom.close()
-    ref = oracle.Sim(oracle.D3Q19, n, n, n, stencil=4, G=-5.0, tau=1.0, coll=coll)
+    ref = oracle.Sim(oracle.D3Q19, n, n, n, stencil=stencil, G=-5.0, tau=1.0, coll=coll)
     ref.init_droplet(2.0, 0.15, 40.0, 2.0)
     ref.step(3)
     f_ref = ref.get_f()
@@ -359,6 +363,7 @@ def test_one_pass_ragged_3d_against_oracle(lbm):
     (1, (8, 9, 136), 4, 1, 1),     # 136: every run-time width, MRT
     (1, (8, 9, 420), 4, 1, 0),     # 420 (one row per item)
     (1, (21, 19, 37), 6, 1, 0),
+    (1, (13, 11, 64), 6, 1, 0),    # radius-2 whole-row kernels (ragged rows and chunks)
     (1, (20, 16, 33), 4, 0, 0),
     (1, (13, 11, 256), 4, 0, 1),
     (0, (1, 45, 300), 4, 1, 0),
