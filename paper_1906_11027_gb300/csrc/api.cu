@@ -149,6 +149,8 @@ struct lbm_ctx {
     int n_cand;
     int cand[kMaxVariants + 1];       // candidate schedules of the autotuner
     double cand_ms[kMaxVariants + 1]; // their measured milliseconds per step
+    float* carry[2];   // carried density of buf[0] / buf[1] (schedules with carry_rows > 0)
+    int carry_tag[2];  // rows per group of the carry layout in carry[i]; 0: not the density of buf[i]
 
     void* dalloc(size_t bytes)
     {
@@ -176,6 +178,8 @@ struct lbm_ctx {
         finish_params(a.p);
         a.fin = buf[cur];
         a.fout = buf[cur ^ 1];
+        a.carry_in = carry[cur];
+        a.carry_out = carry[cur ^ 1];
         a.psi = psi;
         a.tmap = &tmap;
         a.partials = partials;
@@ -202,22 +206,55 @@ int set_device(lbm_ctx* c)
     return LBM_OK;
 }
 
-// Launches schedule v (-1 two-pass, else one-pass variant v) from buffer cur to cur^1.
-int launch_schedule(lbm_ctx* c, int v, const LaunchArgs& a)
+// A schedule with a carried density (carry_rows > 0) reads the density of the
+// current state from carry[cur] and writes that of the next into carry[cur^1].
+// Makes carry[cur] hold the density of buf[cur] in schedule v's layout: the
+// buffers are allocated on first use (for the smallest group among the
+// candidates), and k_carry_init starts a carry whenever carry_tag says that
+// carry[cur] is stale or in another layout.
+int ensure_carry(lbm_ctx* c, int v)
 {
+    const int rows = v >= 0 ? c->ks.onepass[v].carry_rows : 0;
+    if (rows == 0) return LBM_OK;
+    if (!c->ks.carry_init) return fail(LBM_EUNSUPPORTED, "no carried-density kernel for this case");
+    if (!c->carry[0]) {
+        int rmin = rows;
+        for (int i = 0; i < c->n_cand; ++i) {
+            const int r = c->cand[i] >= 0 ? c->ks.onepass[c->cand[i]].carry_rows : 0;
+            if (r > 0 && r < rmin) rmin = r;
+        }
+        const long long nty = (c->prm.ny + rmin - 1) / rmin;
+        const size_t bytes = sizeof(float) * (size_t)(c->N + 2LL * nty * c->prm.nz * c->prm.nx);
+        for (int i = 0; i < 2; ++i) {
+            c->carry[i] = static_cast<float*>(c->dalloc(bytes));
+            if (!c->carry[i]) return fail(LBM_ENOMEM, "carried-density allocation failed");
+        }
+    }
+    if (c->carry_tag[c->cur] != rows) {
+        LBM_CK(c->ks.carry_init(c->args(), rows, c->stream));
+        c->carry_tag[c->cur] = rows;
+    }
+    return LBM_OK;
+}
+
+// Launches schedule v (-1 two-pass, else one-pass variant v) from buffer cur to cur^1.
+int launch_schedule(lbm_ctx* c, int v)
+{
+    if (int rc = ensure_carry(c, v)) return rc;
+    const LaunchArgs a = c->args();
     if (v >= 0) {
         LBM_CK(c->ks.onepass[v].fn(a, c->stream));
     } else {
         LBM_CK(c->ks.psi(a, c->stream));
         LBM_CK(c->ks.fused(a, c->stream));
     }
+    c->carry_tag[c->cur ^ 1] = v >= 0 ? c->ks.onepass[v].carry_rows : 0;
     return LBM_OK;
 }
 
 int one_step(lbm_ctx* c)
 {
-    LaunchArgs a = c->args();
-    if (int rc = launch_schedule(c, c->variant, a)) return rc;
+    if (int rc = launch_schedule(c, c->variant)) return rc;
     c->cur ^= 1;
     return LBM_OK;
 }
@@ -235,15 +272,14 @@ int autotune(lbm_ctx* c)
         cudaEventDestroy(e0);
         return fail(LBM_ECUDA, "event creation failed");
     }
-    const LaunchArgs a = c->args();
     constexpr int kReps = 3;
     int rc = LBM_OK;
     int best = -1;
     for (int i = 0; i < c->n_cand && rc == LBM_OK; ++i) {
         const int v = c->cand[i];
-        rc = launch_schedule(c, v, a);  // warm-up
+        rc = launch_schedule(c, v);  // warm-up (and the start of a carried density)
         if (rc == LBM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = fail(LBM_ECUDA, "event record");
-        for (int r = 0; r < kReps && rc == LBM_OK; ++r) rc = launch_schedule(c, v, a);
+        for (int r = 0; r < kReps && rc == LBM_OK; ++r) rc = launch_schedule(c, v);
         if (rc == LBM_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) rc = fail(LBM_ECUDA, "event record");
         if (rc == LBM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(LBM_ECUDA, "event sync");
         float ms = 0.f;
@@ -325,6 +361,7 @@ int field_mean(lbm_ctx* c, const double* x, double* mean)
 // whenever they change.
 void invalidate_graph(lbm_ctx* c)
 {
+    c->carry_tag[0] = c->carry_tag[1] = 0;  // every caller changes the state or the schedule
     if (c->graph_valid) {
         cudaGraphExecDestroy(c->graph);
         c->graph_valid = false;
@@ -579,6 +616,8 @@ int lbm_destroy(lbm_ctx* c)
     if (c->graph_valid) cudaGraphExecDestroy(c->graph);
     c->dfree(c->buf[0]);
     c->dfree(c->buf[1]);
+    c->dfree(c->carry[0]);
+    c->dfree(c->carry[1]);
     c->dfree(c->psi);
     c->dfree(c->partials);
     c->dfree(c->res);
@@ -783,8 +822,10 @@ int lbm_step(lbm_ctx* c, int64_t n)
         if (int rc = autotune(c)) return rc;
     while (n > 0) {
         if (c->graphs_ok && n >= kGraphSteps && c->cur == 0) {
-            if (!c->graph_valid)
+            if (!c->graph_valid) {
+                if (int rc = ensure_carry(c, c->variant)) return rc;  // outside the capture
                 if (int rc = build_graph(c)) return rc;
+            }
             LBM_CK(cudaGraphLaunch(c->graph, c->stream));
             n -= kGraphSteps;
             c->step += kGraphSteps;
@@ -803,6 +844,7 @@ int lbm_step_timed(lbm_ctx* c, int64_t n, double* mean_ms, int max_kernels, int*
     if (int rc = set_device(c)) return rc;
     if (int rc = autotune(c)) return rc;
     const int K = c->variant >= 0 ? 1 : 2;  // onepass | psi, fused
+    if (int rc = ensure_carry(c, c->variant)) return rc;
     std::vector<cudaEvent_t> ev((size_t)n * K + 1);
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(LBM_ECUDA, "event creation failed");
@@ -822,6 +864,7 @@ int lbm_step_timed(lbm_ctx* c, int64_t n, double* mean_ms, int max_kernels, int*
                     rc = fail(LBM_ECUDA, "fused: %s", cudaGetErrorString(e));
             if (rc == LBM_OK) cudaEventRecord(ev[i * K + 2], c->stream);
         }
+        c->carry_tag[c->cur ^ 1] = c->variant >= 0 ? c->ks.onepass[c->variant].carry_rows : 0;
         c->cur ^= 1;
         c->step += 1;
     }

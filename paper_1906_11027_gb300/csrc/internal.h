@@ -76,6 +76,8 @@ struct LaunchArgs {
     int mode;              // init profile: 0 droplet, 1 flat
     int axis;
     double a0, a1, a2, a3; // init parameters (rho_l, rho_g, R, width)
+    float* carry_in;       // carried density of the current state (schedules with carry_rows > 0)
+    float* carry_out;      // carried density of the state written
 };
 
 // One compiled variant of the one-pass step kernel (tile shape, chunk length,
@@ -86,8 +88,9 @@ struct StepVariant {
     int nx_multiple;     // nx must be a multiple of this (two cells per thread, 16-byte rows)
     int nx_exact;        // nonzero: the variant is compiled for this nx only (whole rows in shared memory)
     int nx_max;          // nonzero: the variant takes rows of at most this many cells (shared-memory size)
+    int carry_rows;      // nonzero: the step reads and writes a carried density for groups of this many rows
 };
-constexpr int kMaxVariants = 40;
+constexpr int kMaxVariants = 48;
 
 // One set of launchers per (lattice, stencil order, collision, precision).
 struct KernelSet {
@@ -104,6 +107,7 @@ struct KernelSet {
     cudaError_t (*get_f)(const LaunchArgs&, cudaStream_t);
     cudaError_t (*set_f)(const LaunchArgs&, cudaStream_t);
     cudaError_t (*rho_of_f)(const LaunchArgs&, cudaStream_t);
+    cudaError_t (*carry_init)(const LaunchArgs&, int rows, cudaStream_t);  // null: no carried-density schedule
 };
 
 // Records msg as the calling thread's lbm_last_error() text and returns code.

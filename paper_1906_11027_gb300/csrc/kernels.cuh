@@ -2216,6 +2216,366 @@ __global__ void __launch_bounds__((NXMAX / 2 * TY + 31) / 32 * 32 + (PRODW ? 32 
     if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
 }
 
+// ---- whole-row schedule with a carried density ------------------------------
+// Position of direction b among the directions with (c_x, c_y) != 0, which
+// cross between the threads of a slab; -1 for the rest.
+template <int LAT>
+__host__ __device__ constexpr int xchg_index(int b)
+{
+    using L = Lattice<LAT>;
+    int k = 0;
+    for (int j = 0; j < b; ++j)
+        if (L::T.v[j][0] != 0 || L::T.v[j][1] != 0) ++k;
+    return (L::T.v[b][0] != 0 || L::T.v[b][1] != 0) ? k : -1;
+}
+template <int LAT>
+__host__ __device__ constexpr int xchg_count()
+{
+    return xchg_index<LAT>(Lattice<LAT>::Q - 1) + 1;
+}
+
+// Carried density of the next step (k_onepass_rowc).  The density deviation
+// rho(x, t+1) - rho_bar = sum_i g_i(x - c_i) of the post-collision values of
+// step t is written by step t itself, so that step t+1 finds the psi of the
+// halo rows without staging their populations.  Rows are grouped TY at a time;
+// a block sums the sources inside its group ("own", one value per cell) and
+// writes what its first and last rows send across the group boundary into two
+// frames:
+//   own  [nz][ny][nx]
+//   lo   [nty][nz][nx]: sent by group g to row y0(g) - 1 (the last row of g - 1)
+//   hi   [nty][nz][nx]: sent by group g to row y0(g) + rows(g) (the first of g + 1)
+// and the density of row y is own + hi[g(y) - 1] (if y is the first row of its
+// group) + lo[g(y) + 1] (if it is the last), summed in that order, with the
+// group indices periodic.  k_carry_init starts a carry from populations: own
+// is the whole sum and both frames are zero.
+struct CarryView {
+    const float* own;
+    const float* lo;
+    const float* hi;
+};
+__host__ __device__ inline long long carry_floats(long long N, int nty, int nz, int nx)
+{
+    return N + 2LL * nty * nz * nx;
+}
+
+template <int LAT>
+__global__ void __launch_bounds__(256)
+    k_carry_init(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, float* __restrict__ c, int nty)
+{
+    using L = Lattice<LAT>;
+    const long long nfr = 2LL * nty * p.nz * p.nx;
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < p.N + nfr; i += stride) {
+        if (i >= p.N) {
+            c[i] = 0.f;
+            continue;
+        }
+        const int x = static_cast<int>(i % p.nx);
+        const int y = static_cast<int>((i / p.nx) % p.ny);
+        const int z = static_cast<int>(i / (static_cast<long long>(p.nx) * p.ny));
+        float s = 0.f;
+        sfor<L::Q>([&](auto bI) {
+            constexpr int b = decltype(bI)::value;
+            constexpr int vx = L::T.v[b][0], vy = L::T.v[b][1], vz = L::T.v[b][2];
+            const int xs = wrap_any(x - vx, p.nx);
+            const int ys = wrap_any(y - vy, p.ny);
+            const int zs = wrap_any(z - vz, p.nz);
+            s += P.in[b][(static_cast<long long>(zs) * p.ny + ys) * p.nx + xs];
+        });
+        c[i] = s;
+    }
+}
+
+// Whole-row packed-pair schedule with a carried density (FP32, 3-D lattices of
+// reach 1, any stencil radius R).  Staging, item walk and packed collision are
+// those of k_onepass_rowp2, with three changes:
+// - psi of slab m + R comes from the carried density of the step before: the
+//   own values plus the frames of the group-boundary rows, loaded one slab
+//   ahead into registers.  A stage holds only the TY rows of the item per
+//   direction, whatever R, so two or three stages fit;
+// - the staged populations collide at once: no delay line;
+// - the block also collides the slab before and the slab after its chunk
+//   (m0 - 1 and m1, not stored), so every slab of the chunk receives all its
+//   sources from this block and no frame crosses a chunk boundary.
+// After the collision of slab m the pairs of the directions that cross between
+// threads go to an exchange buffer; each thread then sums, per c_z, what its two
+// cells receive from slab m (sources outside the group come through the frames),
+// and a two-slab delay in registers completes the carried density of slab m - 1.
+template <int LAT, int ORD, int COLL, int TY, int NSTG, int NXMAX>
+__global__ void __launch_bounds__((NXMAX / 2 * TY + 31) / 32 * 32, 1)
+    k_onepass_rowc(const __grid_constant__ Pops<float, Lattice<LAT>::Q> P, DevParams p, CarryView cin,
+                   float* __restrict__ cout, int zc, int nitems)
+{
+    using L = Lattice<LAT>;
+    using S = Stencil<3, ORD>;
+    constexpr int R = S::radius;
+    constexpr int Q = L::Q;
+    constexpr int NXD = xchg_count<LAT>();
+    static_assert(L::D == 3 && L::reach == 1, "row staging for 3-D reach-1 lattices");
+    constexpr int EY = TY + 2 * R;          // psi rows of the ring
+    constexpr int NS = 2 * R + 1;           // psi slabs of the ring
+    constexpr int KR = (EY + TY - 1) / TY;  // psi rows per thread, at most
+    static_assert((NXMAX / 2 * TY + 31) / 32 * 32 <= 1024 && NXMAX % 4 == 0, "block shape");
+    static_assert(NSTG >= 1 && NSTG <= 32, "stages");
+    const int nx = p.nx;
+    const int half = nx / 2;
+    const int NT = (half * TY + 31) / 32 * 32;  // threads, whole warps
+    const int EX = nx + 2 * R;
+    const int E = EX * EY;
+    const int STG = Q * TY * nx;
+    __shared__ alignas(8) unsigned long long bars[NSTG];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    float* stage = reinterpret_cast<float*>(dyn_smem);  // [NSTG][Q][TY][nx]
+    float* ring = stage + NSTG * STG;                    // [NS][EY][EX]
+    float* xch = ring + NS * E;                          // [NXD][TY][nx]
+
+    const int nty = (p.ny + TY - 1) / TY;
+    const int nm = p.nz;
+    const int plane = nx * p.ny;
+    const long long fsz = static_cast<long long>(nm) * nx;  // one group's frame
+    float* cout_lo = cout + p.N;
+    float* cout_hi = cout_lo + nty * fsz;
+    const int tid = threadIdx.x;
+    const int tp = tid % half, ty = tid / half;  // pair along x, row in the group (ty >= TY: idle lane)
+    const int x0 = 2 * tp;
+    const int lane = tid & 31;
+    const bool issuer = tid / 32 == NT / 32 - 1;
+
+    if (tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    int cby = 0, cbz = 0;
+    const float* src_b = nullptr;
+    sfor<Q>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        constexpr int vy = L::T.v[b][1], vz = L::T.v[b][2];
+        if (lane == b) {
+            cby = vy;
+            cbz = vz;
+            src_b = P.in[b];
+        }
+    });
+    // the copy sequence: for every item of this block, slabs m0 - 1 .. m1
+    int p_it = blockIdx.x, p_y0 = 0, p_next = 0, p_last = -1;
+    auto p_load_item = [&]() {
+        if (p_it >= nitems) return;
+        const int m0 = (p_it / nty) * zc;
+        p_y0 = (p_it % nty) * TY;
+        p_next = m0 - 1;
+        p_last = (m0 + zc < nm) ? m0 + zc : nm;
+    };
+    p_load_item();
+    long long issued = 0;
+    auto issue_next = [&]() {
+        const int slot = static_cast<int>(issued % NSTG);
+        const uint32_t bar = smem_u32(&bars[slot]);
+        if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(STG * sizeof(float)));
+        __syncwarp();
+        if (lane < Q) {
+            fence_proxy_async_smem();
+            const float* pl = src_b + static_cast<long long>(wrap_any(p_next - cbz, nm)) * plane;
+            uint32_t dst = smem_u32(stage + slot * STG + lane * (TY * nx));
+            int y = p_y0 - cby, left = TY;
+            while (left > 0) {
+                const int yw = wrap_any(y, p.ny);
+                const int n = (p.ny - yw < left) ? p.ny - yw : left;
+                bulk_g2s(dst, pl + static_cast<long long>(yw) * nx, static_cast<uint32_t>(n * nx * sizeof(float)), bar);
+                dst += static_cast<uint32_t>(n * nx * sizeof(float));
+                y += n;
+                left -= n;
+            }
+        }
+        __syncwarp();
+        ++issued;
+        if (++p_next > p_last) {
+            p_it += gridDim.x;
+            p_load_item();
+        }
+    };
+    auto issue_upto = [&](long long consumed) {
+        while (p_it < nitems && issued < consumed + NSTG) issue_next();
+    };
+
+    uint32_t phase = 0;
+    bool ok = true;
+    long long consumed = 0;
+    auto wait_seq = [&](long long q) -> const float* {
+        const int slot = static_cast<int>(q % NSTG);
+        if (ok && !mbar_wait(smem_u32(&bars[slot]), (phase >> slot) & 1u)) ok = false;  // after a timeout, stop waiting
+        phase ^= 1u << slot;
+        return stage + slot * STG;
+    };
+    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;  // column x - 1 of the first cell
+    const int xr = (x0 + 2 == nx) ? 0 : x0 + 2;  // column x + 1 of the second cell
+    // the pair's values of a row shifted by -c_x (the pull source of direction c_x)
+    auto pull_row = [&](const float* r, int vx) -> float2 {
+        if (vx == 0) return *reinterpret_cast<const float2*>(r + x0);
+        if (vx > 0) return make_float2(r[xl], r[x0]);
+        return make_float2(r[x0 + 1], r[xr]);
+    };
+    // the three parts (own, frame from the group before, frame from the group
+    // after) of the carried density of grid row yr, slab z, for the pair
+    auto carry_load = [&](int yr, int z, float2 (&v)[3]) {
+        const int gr = yr / TY;
+        const int first = gr * TY;
+        const int last = ((first + TY < p.ny) ? first + TY : p.ny) - 1;
+        const long long fz = static_cast<long long>(z) * nx + x0;
+        v[0] = __ldg(reinterpret_cast<const float2*>(cin.own + static_cast<long long>(z) * plane + yr * nx + x0));
+        v[1] = p2(0.f);
+        v[2] = p2(0.f);
+        if (yr == first) v[1] = __ldg(reinterpret_cast<const float2*>(cin.hi + (gr == 0 ? nty - 1 : gr - 1) * fsz + fz));
+        if (yr == last) v[2] = __ldg(reinterpret_cast<const float2*>(cin.lo + (gr + 1 == nty ? 0 : gr + 1) * fsz + fz));
+    };
+    // carried densities of the thread's psi rows (ring rows ty, ty + TY, ...) of slab s
+    auto psi_load = [&](int y0, int s, float2 (&v)[KR][3]) {
+        const int z = wrap_any(s, nm);
+#pragma unroll
+        for (int j = 0; j < KR; ++j) {
+            const int k = ty + j * TY;
+            if (k < EY) carry_load(wrap_any(y0 - R + k, p.ny), z, v[j]);
+        }
+    };
+    // psi of the pair into ring row fy, and into the R wrapped columns on each side
+    auto put_psi2 = [&](float* dst, int fy, float2 v) {
+        float* row = dst + fy * EX;
+        row[x0 + R] = v.x;
+        row[x0 + 1 + R] = v.y;
+        if (x0 < R) {
+            row[x0 + nx + R] = v.x;
+            if (x0 + 1 < R) row[x0 + 1 + nx + R] = v.y;
+        }
+        if (x0 + 1 >= nx - R) {
+            row[x0 + 1 - nx + R] = v.y;
+            if (x0 >= nx - R) row[x0 - nx + R] = v.x;
+        }
+    };
+    auto psi_put = [&](int s, const float2 (&v)[KR][3]) {
+        float* dst = ring + ring_slot(s, NS) * E;
+#pragma unroll
+        for (int j = 0; j < KR; ++j) {
+            const int k = ty + j * TY;
+            if (k < EY) {
+                const float2 r = add2(add2(v[j][0], v[j][1]), v[j][2]);
+                put_psi2(dst, k, make_float2(psi_of<LAT>(p.rho_bar_f + r.x, p), psi_of<LAT>(p.rho_bar_f + r.y, p)));
+            }
+        }
+    };
+
+    float2 pre[KR][3];
+    if (issuer) issue_upto(0);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int g = it % nty;
+        const int y0 = g * TY;
+        const int rows = (y0 + TY < p.ny) ? TY : p.ny - y0;
+        const int m0 = (it / nty) * zc;
+        const int m1 = (m0 + zc < nm) ? m0 + zc : nm;
+        const bool act = ty < rows;
+        const bool top = ty == 0, bot = ty == rows - 1;
+        // warm-up: psi of slabs m0 - 1 - R .. m0 - 2 + R into the ring, slab
+        // m0 - 1 + R into the registers (all loads issued before the first use)
+        if (ty < TY) {
+            float2 w[2 * R][KR][3];
+#pragma unroll
+            for (int k = 0; k < 2 * R; ++k) psi_load(y0, m0 - 1 - R + k, w[k]);
+            psi_load(y0, m0 - 1 + R, pre);
+#pragma unroll
+            for (int k = 0; k < 2 * R; ++k) psi_put(m0 - 1 - R + k, w[k]);
+        }
+        float2 A0 = p2(0.f), A1 = p2(0.f), U0 = p2(0.f), U1 = p2(0.f), V0 = p2(0.f), V1 = p2(0.f);
+        const long long cell_xy = static_cast<long long>(y0 + ty) * nx + x0;
+        for (int m = m0 - 1; m <= m1; ++m) {
+            if (ty < TY) {
+                psi_put(m + R, pre);
+                if (m < m1) psi_load(y0, m + R + 1, pre);
+            }
+            const float* st = wait_seq(consumed);
+            float2 f[Q];
+            if (act) {
+                const float* r = st + ty * nx;
+                sfor<Q>([&](auto bI) {
+                    constexpr int b = decltype(bI)::value;
+                    constexpr int vx = L::T.v[b][0];
+                    f[b] = pull_row(r + b * (TY * nx), vx);
+                });
+            }
+            ++consumed;
+            __syncthreads();  // psi of slab m + R in the ring; the stage slot is free
+            if (issuer) issue_upto(consumed);
+            if (act) {
+                // force (Eq. 1) of both cells from the psi ring, opposite vectors paired
+                const float* base[2 * R + 1];
+#pragma unroll
+                for (int k = 0; k < 2 * R + 1; ++k) base[k] = ring + ring_slot(m - R + k, NS) * E + (ty + R) * EX + x0 + R;
+                float2 ax = p2(0.f), ay = p2(0.f), az = p2(0.f);
+                sfor<S::n / 2>([&](auto kI) {
+                    constexpr int a = 2 * decltype(kI)::value;
+                    constexpr int ex = S::T.v[a][0], ey = S::T.v[a][1], ez = S::T.v[a][2];
+                    constexpr double wt = S::T.w[a] * L::cs2;
+                    const float* pp = base[ez + R] + ey * EX + ex;
+                    const float* pm = base[R - ez] - ey * EX - ex;
+                    const float2 d = sub2(make_float2(pp[0], pp[1]), make_float2(pm[0], pm[1]));
+                    if (ex != 0) ax = fma2(p2(float(wt * ex)), d, ax);
+                    if (ey != 0) ay = fma2(p2(float(wt * ey)), d, ay);
+                    if (ez != 0) az = fma2(p2(float(wt * ez)), d, az);
+                });
+                const float2 gp = mul2(p2(-p.G_f), make_float2(base[R][0], base[R][1]));
+                const float2 F[3] = {mul2(gp, ax), mul2(gp, ay), mul2(gp, az)};
+                collide2<LAT, COLL>(f, F, p);
+                if (m >= m0 && m < m1) {
+                    const long long c = static_cast<long long>(m) * plane + cell_xy;
+                    sfor<Q>([&](auto bI) {
+                        constexpr int b = decltype(bI)::value;
+                        __stcs(reinterpret_cast<float2*>(P.out[b] + c), f[b]);
+                    });
+                }
+                sfor<Q>([&](auto bI) {
+                    constexpr int b = decltype(bI)::value;
+                    constexpr int xi = xchg_index<LAT>(b);
+                    if constexpr (xi >= 0) *reinterpret_cast<float2*>(xch + (xi * TY + ty) * nx + x0) = f[b];
+                });
+            }
+            __syncthreads();  // the exchange buffer holds slab m
+            if (act) {
+                // what the pair receives from slab m, per c_z (T), and what rows
+                // y0 - 1 (U) and y0 + rows (V) receive from the group's edge rows
+                float2 T[3] = {p2(0.f), p2(0.f), p2(0.f)};
+                float2 Uc[3] = {p2(0.f), p2(0.f), p2(0.f)};
+                float2 Vc[3] = {p2(0.f), p2(0.f), p2(0.f)};
+                sfor<Q>([&](auto bI) {
+                    constexpr int b = decltype(bI)::value;
+                    constexpr int vx = L::T.v[b][0], vy = L::T.v[b][1], vz = L::T.v[b][2];
+                    constexpr int xi = xchg_index<LAT>(b);
+                    if constexpr (xi < 0) {
+                        T[vz + 1] = add2(T[vz + 1], f[b]);
+                    } else {
+                        const float* xb = xch + xi * TY * nx;
+                        const int sy = ty - vy;
+                        if (sy >= 0 && sy < rows) T[vz + 1] = add2(T[vz + 1], pull_row(xb + sy * nx, vx));
+                        if (vy < 0 && top) Uc[vz + 1] = add2(Uc[vz + 1], pull_row(xb, vx));
+                        if (vy > 0 && bot) Vc[vz + 1] = add2(Vc[vz + 1], pull_row(xb + (rows - 1) * nx, vx));
+                    }
+                });
+                if (m - 1 >= m0 && m - 1 < m1) {  // slab m - 1 has received all its sources
+                    const long long fo = static_cast<long long>(g) * fsz + static_cast<long long>(m - 1) * nx + x0;
+                    *reinterpret_cast<float2*>(cout + static_cast<long long>(m - 1) * plane + cell_xy) = add2(A0, T[0]);
+                    if (top) *reinterpret_cast<float2*>(cout_lo + fo) = add2(U0, Uc[0]);
+                    if (bot) *reinterpret_cast<float2*>(cout_hi + fo) = add2(V0, Vc[0]);
+                }
+                A0 = add2(A1, T[1]);
+                A1 = T[2];
+                U0 = add2(U1, Uc[1]);
+                U1 = Uc[2];
+                V0 = add2(V1, Vc[1]);
+                V1 = Vc[2];
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicOr(p.err, kErrTimeout);
+}
+
 // Packed-pair form of the segment schedule k_onepass_seg (FP32 BGK, 2-D reach-1
 // lattices): a compute thread owns the x-adjacent cells (2t, 2t + 1) of the
 // tile, so the directions with c_x = 0 come from the staged segment as one
@@ -3029,6 +3389,52 @@ cudaError_t launch_onepass_rowr(const LaunchArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Whole-row schedule with a carried density (k_onepass_rowc), any row length
+// nx <= NXMAX that is a multiple of 4.  Reads the carry of the current state
+// (a.carry_in) and writes that of the next (a.carry_out).
+template <int LAT, int ORD, int COLL, int NXMAX, int TY, int NSTG>
+cudaError_t launch_onepass_rowc(const LaunchArgs& a, cudaStream_t s)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    constexpr int R = Stencil<3, ORD>::radius;
+    constexpr int EY = TY + 2 * R;
+    constexpr int NS = 2 * R + 1;
+    constexpr int NXD = xchg_count<LAT>();
+    auto dyn_of = [](int nx) {
+        return sizeof(float) * (static_cast<size_t>(NSTG) * Q * TY * nx + static_cast<size_t>(NS) * (nx + 2 * R) * EY +
+                                static_cast<size_t>(NXD) * TY * nx);
+    };
+    auto kern = &k_onepass_rowc<LAT, ORD, COLL, TY, NSTG, NXMAX>;
+    if (cudaError_t e = ensure_dyn_smem(kern, dyn_of(NXMAX)); e != cudaSuccess) return e;
+    const int nx = a.p.nx;
+    if (nx % 4 != 0 || nx < 8 || nx > NXMAX || !a.carry_in || !a.carry_out) return cudaErrorInvalidValue;
+    const int nty = (a.p.ny + TY - 1) / TY;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int zc = rowp_chunk(a.p.nz, nty, nsm, 2);
+    const int nitems = nty * ((a.p.nz + zc - 1) / zc);
+    const int grid = nitems < nsm ? nitems : nsm;
+    const int threads = (nx / 2 * TY + 31) / 32 * 32;
+    const long long fr = static_cast<long long>(nty) * a.p.nz * nx;
+    const CarryView cv{a.carry_in, a.carry_in + a.p.N, a.carry_in + a.p.N + fr};
+    const auto P = make_pops<float, Q>(a.fin, a.fout, a.p.N);
+    kern<<<grid, threads, dyn_of(nx), s>>>(P, a.p, cv, a.carry_out, zc, nitems);
+    return cudaGetLastError();
+}
+
+// Starts the carry of the current state (a.fin) in a.carry_in for groups of ty
+// rows: own = the whole pulled sum, frames zero.
+template <int LAT>
+cudaError_t launch_carry_init(const LaunchArgs& a, int ty, cudaStream_t s)
+{
+    if (!a.carry_in || ty < 1) return cudaErrorInvalidValue;
+    const int nty = (a.p.ny + ty - 1) / ty;
+    const auto P = make_pops<float, Lattice<LAT>::Q>(a.fin, a.fout, a.p.N);
+    k_carry_init<LAT><<<grid_1d(carry_floats(a.p.N, nty, a.p.nz, a.p.nx)), 256, 0, s>>>(P, a.p, a.carry_in, nty);
+    return cudaGetLastError();
+}
+
 template <int LAT, int ORD, int COLL, class Real, int NX, int TY, int NSTG>
 cudaError_t launch_onepass_rowp(const LaunchArgs& a, cudaStream_t s)
 {
@@ -3246,7 +3652,7 @@ constexpr VariantList make_variants()
     constexpr bool k3 = Lattice<LAT>::D == 3;
     VariantList k{};
     auto add = [&k](const char* name, cudaError_t (*fn)(const LaunchArgs&, cudaStream_t), int nx_mult = 1,
-                    int nx_exact = 0, int nx_max = 0) {
+                    int nx_exact = 0, int nx_max = 0, int carry_rows = 0) {
         if (k.n >= kMaxVariants) {
             k.overflow = true;
             return;
@@ -3256,6 +3662,7 @@ constexpr VariantList make_variants()
         k.v[k.n].nx_multiple = nx_mult;
         k.v[k.n].nx_exact = nx_exact;
         k.v[k.n].nx_max = nx_max;
+        k.v[k.n].carry_rows = carry_rows;
         ++k.n;
     };
     constexpr bool r1 = Stencil<Lattice<LAT>::D, ORD>::radius == 1;
@@ -3303,6 +3710,10 @@ constexpr VariantList make_variants()
                 add("onepass_rowr_w256x3_s1_np", &launch_onepass_rowr<LAT, ORD, COLL, 256, 3, 1, false>, 4, 0, 256);
                 add("onepass_rowr_w256x1_s2", &launch_onepass_rowr<LAT, ORD, COLL, 256, 1, 2, true>, 4, 0, 256);
             }
+            if constexpr (Lattice<LAT>::reach == 1) {
+                add("onepass_rowc_w256x3_s2", &launch_onepass_rowc<LAT, ORD, COLL, 256, 3, 2>, 4, 0, 256, 3);
+                add("onepass_rowc_w256x2_s3", &launch_onepass_rowc<LAT, ORD, COLL, 256, 2, 3>, 4, 0, 256, 2);
+            }
             add("onepass_la_32x8_z16_b2", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 2, 1>);
             add("onepass_lai_32x8_z16_b3", &launch_onepass_la<LAT, ORD, COLL, Real, 32, 8, 16, 3, 0>);
             add("onepass_x2_64x8_z16_b2_smem", &launch_onepass_x2<LAT, ORD, 32, 8, 16, 2, 2>, 2);
@@ -3317,6 +3728,11 @@ constexpr VariantList make_variants()
             add("onepass_rowp2_w208x2_s3", &launch_onepass_rowp2w<LAT, ORD, 1, 208, 2, 3, true>, 4, 0, 208);
             add("onepass_rowp2_w344x2_s2", &launch_onepass_rowp2w<LAT, ORD, 1, 344, 2, 2, true>, 4, 0, 344);
             add("onepass_rowp2_w456x1_s2", &launch_onepass_rowp2w<LAT, ORD, 1, 456, 1, 2, true>, 4, 0, 456);
+        }
+        // MRT in FP32, any stencil radius: the carried-density whole-row kernels
+        if constexpr (COLL == 1 && std::is_same<Real, float>::value && Lattice<LAT>::reach == 1) {
+            add("onepass_rowc_w256x3_s2", &launch_onepass_rowc<LAT, ORD, 1, 256, 3, 2>, 4, 0, 256, 3);
+            add("onepass_rowc_w256x2_s3", &launch_onepass_rowc<LAT, ORD, 1, 256, 2, 3>, 4, 0, 256, 2);
         }
     } else {
         add("onepass_128_z16_b2_smem", &launch_onepass<LAT, ORD, COLL, Real, 128, 1, 16, 2, 2>);
@@ -3369,6 +3785,7 @@ KernelSet make_set()
     k.get_f = &launch_get_f<LAT, Real>;
     k.set_f = &launch_set_f<LAT, Real>;
     k.rho_of_f = &launch_rho_of_f<LAT>;
+    if constexpr (k3 && std::is_same<Real, float>::value) k.carry_init = &launch_carry_init<LAT>;
     return k;
 }
 

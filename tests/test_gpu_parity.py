@@ -293,13 +293,16 @@ def test_full_size_d3q19_256_fp32_against_oracle(lbm):
 
 @pytest.mark.parametrize("coll,stencil,schedule", [(0, 4, "onepass_rowp2_256x3_s2_np"),
                                                   (1, 4, "onepass_rowp2_256x3_s2_np"),
-                                                  (0, 6, "onepass_rowr_w256x3_s1_np")])
+                                                  (0, 6, "onepass_rowr_w256x3_s1_np"),
+                                                  (0, 6, "onepass_rowc_w256x3_s2"),
+                                                  (1, 6, "onepass_rowc_w256x3_s2")])
 def test_full_size_headline_schedule_populations_against_oracle(lbm, coll, stencil, schedule):
     """The benchmark's schedule at the benchmark's size, populations compared
     cell by cell: D3Q19, FP32 deviations, 256^3, psi = 1 - exp(-rho), G = -5,
     4th-order stencil, droplet R = 40, with the packed-pair whole-row kernel
     (three rows per item, no producer warp) pinned, BGK and MRT; and the
-    6th-order stencil on the radius-2 whole-row kernel (one stage).  At this
+    6th-order stencil on the radius-2 whole-row kernel (one stage) and on the
+    carried-density kernel (BGK and MRT).  At this
     size every block walks several items, so the copy sequence runs on across
     item boundaries.  After three steps every population lies within 2e-6 of
     the largest (FP32 storage of deviations of size ~0.3, rounded at 2^-24)."""
@@ -318,6 +321,43 @@ def test_full_size_headline_schedule_populations_against_oracle(lbm, coll, stenc
     del ref
     err = np.abs(f_gpu - f_ref).max() / np.abs(f_ref).max()
     assert err <= 2e-6, err
+
+
+@pytest.mark.parametrize("schedule", ["onepass_rowc_w256x3_s2", "onepass_rowc_w256x2_s3"])
+def test_carried_density_restarts_on_every_state_change(lbm, tmp_path, schedule):
+    """The carried-density schedules take psi from a density that the step
+    before wrote for them.  Every change of the state must start that density
+    again from the populations: populations set from the host, a checkpoint
+    loaded, another schedule run in between.  A stale carry would give psi of
+    the state before the change, far outside the FP32 budget checked here."""
+    nz, ny, nx = 12, 13, 64
+    ref = oracle.Sim(oracle.D3Q19, nx, ny, nz, stencil=6, G=-5.0, tau=0.9)
+    ref.init_droplet(1.9, 0.15, 4.0, 2.0)
+    ref.step(4)
+    f4 = ref.get_f()
+    snaps = {}
+    for t in (10, 13, 15):
+        ref.step(t - ref.step_count)
+        snaps[t] = ref.get_f()
+    dom = lbm.Domain(nx, ny, nz, lattice=lbm.LBM_D3Q19, stencil=6, precision=1, G=-5.0, tau=0.9)
+    dom.set_schedule(schedule)
+    dom.init_droplet(1.7, 0.2, 3.0, 2.0)  # another state first, so that a carry of it exists
+    dom.step(3)
+    dom.set_f(f4)
+    dom.step(6)
+    assert rel_max(dom.get_f(), snaps[10]) <= 1e-5
+    ck = str(tmp_path / "state.bin")
+    dom.save(ck)
+    dom.step(5)
+    dom.load(ck)
+    dom.step(3)
+    assert rel_max(dom.get_f(), snaps[13]) <= 1e-5
+    dom.set_schedule("two_pass")
+    dom.step(1)
+    dom.set_schedule(schedule)
+    dom.step(1)
+    assert rel_max(dom.get_f(), snaps[15]) <= 1e-5
+    dom.close()
 
 
 @pytest.mark.parametrize("lattice,shape,stencil,coll,precision", [
@@ -364,6 +404,8 @@ def test_one_pass_ragged_3d_against_oracle(lbm):
     (1, (8, 9, 420), 4, 1, 0),     # 420 (one row per item)
     (1, (21, 19, 37), 6, 1, 0),
     (1, (13, 11, 64), 6, 1, 0),    # radius-2 whole-row kernels (ragged rows and chunks)
+    (1, (13, 11, 64), 6, 1, 1),    # MRT with the 6th-order stencil (carried-density kernels)
+    (1, (10, 13, 96), 6, 1, 0),    # groups of one row (13 = 4 * 3 + 1 = 6 * 2 + 1): both frames on one row
     (1, (20, 16, 33), 4, 0, 0),
     (1, (13, 11, 256), 4, 0, 1),
     (0, (1, 45, 300), 4, 1, 0),
