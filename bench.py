@@ -37,6 +37,9 @@ WORKLOADS = {
     "d3q19_256_fp32_iso6": dict(lattice=1, shape=(256, 256, 256), precision=1, stencil=6, R=40.0,
                                 desc="D3Q19 BGK FP32-shifted 256^3 periodic, psi=1-exp(-rho), G=-5, "
                                      "6th-order 3-D force stencil, centred droplet R=40"),
+    "d3q19_256_fp32_mrt_iso6": dict(lattice=1, shape=(256, 256, 256), precision=1, stencil=6, R=40.0, collision=1,
+                                    desc="D3Q19 MRT (rates 1/tau, s_e=1.64, s_eps=1.54, s_q=1.9) FP32-shifted 256^3 "
+                                         "periodic, psi=1-exp(-rho), G=-5, 6th-order 3-D force stencil, centred droplet R=40"),
     "d3q19_256_fp32_mrt": dict(lattice=1, shape=(256, 256, 256), precision=1, stencil=4, R=40.0, collision=1,
                                desc="D3Q19 MRT (rates 1/tau, s_e=1.64, s_eps=1.54, s_q=1.9) FP32-shifted 256^3 "
                                     "periodic, psi=1-exp(-rho), G=-5, 4th-order 3-D force stencil, centred droplet R=40"),

@@ -3734,6 +3734,9 @@ constexpr VariantList make_variants()
             add("onepass_rowc_w256x3_s2", &launch_onepass_rowc<LAT, ORD, 1, 256, 3, 2>, 4, 0, 256, 3);
             add("onepass_rowc_w256x2_s3", &launch_onepass_rowc<LAT, ORD, 1, 256, 2, 3>, 4, 0, 256, 2);
         }
+        // MRT in FP32 with the radius-2 stencil: the radius-2 whole-row kernel
+        if constexpr (COLL == 1 && std::is_same<Real, float>::value && Stencil<3, ORD>::radius == 2)
+            add("onepass_rowr_w256x3_s1_np", &launch_onepass_rowr<LAT, ORD, 1, 256, 3, 1, false>, 4, 0, 256);
     } else {
         add("onepass_128_z16_b2_smem", &launch_onepass<LAT, ORD, COLL, Real, 128, 1, 16, 2, 2>);
         if constexpr (hot) {

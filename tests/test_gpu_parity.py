@@ -294,6 +294,7 @@ def test_full_size_d3q19_256_fp32_against_oracle(lbm):
 @pytest.mark.parametrize("coll,stencil,schedule", [(0, 4, "onepass_rowp2_256x3_s2_np"),
                                                   (1, 4, "onepass_rowp2_256x3_s2_np"),
                                                   (0, 6, "onepass_rowr_w256x3_s1_np"),
+                                                  (1, 6, "onepass_rowr_w256x3_s1_np"),
                                                   (0, 6, "onepass_rowc_w256x3_s2"),
                                                   (1, 6, "onepass_rowc_w256x3_s2")])
 def test_full_size_headline_schedule_populations_against_oracle(lbm, coll, stencil, schedule):
@@ -302,7 +303,7 @@ def test_full_size_headline_schedule_populations_against_oracle(lbm, coll, stenc
     4th-order stencil, droplet R = 40, with the packed-pair whole-row kernel
     (three rows per item, no producer warp) pinned, BGK and MRT; and the
     6th-order stencil on the radius-2 whole-row kernel (one stage) and on the
-    carried-density kernel (BGK and MRT).  At this
+    carried-density kernel, BGK and MRT.  At this
     size every block walks several items, so the copy sequence runs on across
     item boundaries.  After three steps every population lies within 2e-6 of
     the largest (FP32 storage of deviations of size ~0.3, rounded at 2^-24)."""
