@@ -465,7 +465,8 @@ def sweep_compare(args, n_domains, with_warm, train_domains, epochs, details):
                 and warm["steps"][i] < args.sweep_max_steps]
         arms.update({"batched_fp32_warm_s": round(warm["t"], 3), "warm_init_s": round(warm["t_init"], 3),
                      "warm_fp32_phase_s": round(warm["t_fp32"], 3),
-                     "warm_fallbacks": warm["fallbacks"], "steps_total_warm": int(sum(warm["steps"])),
+                     "warm_fallbacks": warm["fallbacks"], "warm_restarted_from_tanh": warm["restarted"],
+                     "steps_total_warm": int(sum(warm["steps"])),
                      "converged_in_both": len(both),
                      "steps_converged_in_both": {"tanh": int(sum(plain["steps"][i] for i in both)),
                                                  "warm": int(sum(warm["steps"][i] for i in both))}})
@@ -526,6 +527,7 @@ def sweep_summary(args):
         "steps_total": {"tanh_fp32": a["steps_total_tanh"], "warm_fp32": a["steps_total_warm"],
                         "fp64": ln["steps"]["fp64_total"]},
         "steps_converged_in_both": a["steps_converged_in_both"],
+        "warm_restarted_from_tanh": a["warm_restarted_from_tanh"],
         "agreement_classes_warm_vs_fp64": ln["max_u_rel_diff"]["classes"],
         "agreement_classes_tanh_vs_fp64": ln["max_u_rel_diff_tanh_fp32_vs_fp64"]["classes"],
         "warm_start_training": ln["warm_start_training"],

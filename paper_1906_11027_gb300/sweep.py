@@ -4,10 +4,12 @@ Arms (each runs every domain of the draw to steady state under the same rule,
 |max|u|(t) - max|u|(t - K)| / K < tol checked every K = 100 steps, FP32 storage
 adding the floor 1e-6 max|u| / K for its round-off):
 - batched: every domain in one persistent-kernel CUDA graph with FP32
-  deviation storage, from the tanh start or from the learned warm start.  A
-  domain whose steady max|u| is below FP32's velocity resolution (fp64_below)
-  is continued in FP64 from its FP32 state (the precision policy of the
-  batched sweep);
+  deviation storage, from the tanh start or from the learned warm start.  The
+  tanh start is the learned start's fallback: a domain that diverges from the
+  learned start runs again from the tanh start, its steps and time counted in
+  the learned-start arm.  A domain whose steady max|u| is below FP32's
+  velocity resolution (fp64_below) is continued in FP64 from its FP32 state
+  (the precision policy of the batched sweep);
 - one_per_launch: the plain method, one FP64 domain per launch, tanh start.
 
 Agreement rule: a domain's steady max|u| in a batched arm agrees with the FP64
@@ -63,24 +65,42 @@ def batched(doms, net=None, max_steps=200000, fp64_below=FP64_BELOW):
     fallbacks = warmstart.batch_warm_init(b, doms, net) if net is not None else None
     t_init = time.perf_counter() - t0
     steps, obs, ok = b.run_to_steady(TOL, max_steps, K)
+    steps, obs = list(steps), list(obs)
+    evolved = list(steps)  # steps of the run that produced each final state
+    states64 = {}  # final states kept outside the batch
+    restarted = []
+    if net is not None:
+        # the tanh start is the learned start's fallback: a domain that diverged
+        # from the learned start runs again from the tanh start (its steps add up)
+        restarted = [i for i, o in enumerate(obs) if not np.isfinite(o["max_u"])]
+        if restarted:
+            br = lbm.Batch([doms[i] for i in restarted], precision=lbm.LBM_FP32_SHIFTED)
+            sr, orr, okr = br.run_to_steady(TOL, max_steps, K)
+            ok = ok and okr
+            for j, i in enumerate(restarted):
+                steps[i] += sr[j]
+                evolved[i] = sr[j]
+                obs[i] = orr[j]
+                states64[i] = br.get_f(j)
+            br.close()
     _sync()
     t_fp32 = time.perf_counter() - t0
     tiny = [i for i, o in enumerate(obs) if np.isfinite(o["max_u"]) and o["max_u"] < fp64_below]
-    states64 = {}
     if tiny:
         b64 = lbm.Batch([doms[i] for i in tiny], precision=lbm.LBM_FP64)
         for j, i in enumerate(tiny):
-            b64.set_f(j, b.get_f(i))
+            b64.set_f(j, states64[i] if i in states64 else b.get_f(i))
         s64, o64, _ = b64.run_to_steady(TOL, max_steps, K)
         for j, i in enumerate(tiny):
             steps[i] += s64[j]
+            evolved[i] += s64[j]
             obs[i] = o64[j]
             states64[i] = b64.get_f(j)
         b64.close()
     _sync()
-    return dict(t=time.perf_counter() - t0, t_init=t_init, t_fp32=t_fp32, steps=list(steps), obs=list(obs),
-                ok=ok, tiny=len(tiny), fallbacks=fallbacks, schedule=b.schedule_report(), batch=b,
-                states64=states64)
+    return dict(t=time.perf_counter() - t0, t_init=t_init, t_fp32=t_fp32, steps=list(steps), evolved=evolved,
+                obs=list(obs), ok=ok, tiny=len(tiny), fallbacks=fallbacks, restarted=len(restarted), schedule=b.schedule_report(),
+                batch=b, states64=states64)
 
 
 def batched_state(arm, i):
@@ -143,7 +163,7 @@ def classify(doms, arm, ref, fp64_below=FP64_BELOW, tanh_arm=None):
         elif min(ua, ub) < fp64_below:
             out.append("other_basin")
         else:
-            sa, sb = arm["steps"][i], ref["steps"][i]
+            sa, sb = arm.get("evolved", arm["steps"])[i], ref["steps"][i]
             if sa < sb:
                 u = _continued_max_u(d, batched_state(arm, i), sb - sa)
                 ok = abs(u / ub - 1.0) <= 0.05

@@ -63,3 +63,66 @@ def test_keep_states_only_for_misses():
     assert keep(1, 1.01e-3)      # the second arm misses
     assert keep(2, 1e-3)         # the first arm diverged
     assert keep(0, math.inf)
+
+
+class _FakeBatch:
+    """Stands in for lbm.Batch: every domain's outcome is scripted by its "i"."""
+    script = {}   # (precision, i) -> (steps, max_u)
+    made = []
+
+    def __init__(self, doms, precision=None):
+        self.doms, self.precision = doms, precision
+        _FakeBatch.made.append(([d["i"] for d in doms], precision))
+
+    def run_to_steady(self, tol, max_steps, k):
+        out = [self.script[(self.precision, d["i"])] for d in self.doms]
+        return [s for s, _ in out], [{"max_u": u} for _, u in out], True
+
+    def get_f(self, j):
+        return ("f", self.precision, self.doms[j]["i"])
+
+    def set_f(self, j, f):
+        pass
+
+    def close(self):
+        pass
+
+    def schedule_report(self):
+        return {}
+
+
+def test_learned_start_that_diverges_runs_again_from_tanh(monkeypatch):
+    from paper_1906_11027_gb300 import lbm, warmstart
+    monkeypatch.setattr(lbm, "Batch", _FakeBatch)
+    monkeypatch.setattr(warmstart, "batch_warm_init", lambda b, doms, net: 0)
+    monkeypatch.setattr(sweep, "_sync", lambda: None)
+    _FakeBatch.made = []
+    F32, F64 = lbm.LBM_FP32_SHIFTED, lbm.LBM_FP64
+    # domain 0 settles from the learned start; domain 1 diverges from it after
+    # 100 steps and settles from the tanh start in 6000; domain 2 diverges from both
+    _FakeBatch.script = {(F32, 0): (5000, 1e-3), (F32, 1): (100, INF), (F32, 2): (200, INF)}
+    first = dict(_FakeBatch.script)
+    runs = {"n": 0}
+
+    def run(self, tol, max_steps, k):
+        runs["n"] += 1
+        if runs["n"] == 2:  # the restart batch of the diverged domains
+            self.script = {(F32, 1): (6000, 2e-3), (F32, 2): (300, INF)}
+        else:
+            self.script = first
+        return _FakeBatch.__dict__["_run"](self, tol, max_steps, k)
+
+    monkeypatch.setattr(_FakeBatch, "_run", _FakeBatch.run_to_steady, raising=False)
+    monkeypatch.setattr(_FakeBatch, "run_to_steady", run)
+    doms = [{"i": i} for i in range(3)]
+    arm = sweep.batched(doms, net=object())
+    assert [m[0] for m in _FakeBatch.made] == [[0, 1, 2], [1, 2]]
+    assert arm["restarted"] == 2
+    assert arm["steps"] == [5000, 6100, 500]          # the diverged prefix counts
+    assert arm["evolved"] == [5000, 6000, 300]        # the final state's own run
+    assert [o["max_u"] for o in arm["obs"]] == [1e-3, 2e-3, INF]
+    assert sweep.batched_state(arm, 1) == ("f", F32, 1)
+    # from the tanh start nothing is restarted
+    _FakeBatch.made, runs["n"] = [], 0
+    arm = sweep.batched(doms)
+    assert arm["restarted"] == 0 and [m[0] for m in _FakeBatch.made] == [[0, 1, 2]]
